@@ -1,0 +1,277 @@
+"""CPU oracle for the point rasterizer — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package. The GPU
+library never calls it, and it shares no code with the library: it is a plain
+restatement of the paper's method in C (``pcr_oracle.c``, compiled with
+``-ffp-contract=off``) wrapped with ctypes.
+
+Function map (paper sections):
+  quantize30 / split_words / decode_words   Eq. 1, Listing 2, Sec. 3.3
+  morton_code / encode                      Sec. 3.1
+  project_position / project_point          Listing 1
+  select_k                                  Sec. 3.3 (precision threshold)
+  cull                                      Sec. 3.2 (batch frustum culling)
+  render / render_threaded / brute_force    Sec. 3.2-3.3 geometry pass
+  resolve                                   Sec. 3.3 visibility buffer
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import platform
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["pcr_oracle.c", "pcr_oracle.h"]
+_lock = threading.Lock()
+_lib = None
+
+EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
+BATCH_DTYPE = np.dtype([("min", "<f4", (3,)), ("size", "<f4", (3,)),
+                        ("first", "<u4"), ("count", "<u4")])
+assert BATCH_DTYPE.itemsize == 32
+
+
+def _stamp() -> str:
+    h = hashlib.sha256(platform.machine().encode())
+    for s in _SOURCES:
+        with open(os.path.join(_HERE, s), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no FMA contraction, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stamp_file = os.path.join(_BUILD, "stamp")
+    st = _stamp()
+    if not force and os.path.exists(_SO) and os.path.exists(stamp_file):
+        with open(stamp_file) as f:
+            if f.read() == st:
+                return _SO
+    tmp = _SO + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread",
+                           "-ffp-contract=off", "-fno-fast-math", "-o", tmp,
+                           os.path.join(_HERE, "pcr_oracle.c"), "-lm"])
+    os.replace(tmp, _SO)
+    with open(stamp_file, "w") as f:
+        f.write(st)
+    return _SO
+
+
+class View(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_float * 16), ("width", ctypes.c_uint32),
+                ("height", ctypes.c_uint32), ("cull", ctypes.c_int),
+                ("force_k", ctypes.c_int), ("threshold_px", ctypes.c_float)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("batches_rendered", ctypes.c_uint64),
+                ("points_processed", ctypes.c_uint64),
+                ("batches_k", ctypes.c_uint64 * 4), ("points_k", ctypes.c_uint64 * 4),
+                ("points_accepted", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {"batches_rendered": self.batches_rendered,
+                "points_processed": self.points_processed,
+                "batches_k": list(self.batches_k), "points_k": list(self.points_k),
+                "points_accepted": self.points_accepted}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            # PCR_ORACLE_SO lets the mutation test load a copy of the oracle
+            # with a planted mistake; normally the in-tree build is used.
+            path = os.environ.get("PCR_ORACLE_SO") or build()
+            L = ctypes.CDLL(path)
+            vp, u32, u64, f32, i32 = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                      ctypes.c_float, ctypes.c_int)
+            VP = ctypes.POINTER(View)
+            SP = ctypes.POINTER(Stats)
+            L.or_quantize30.argtypes = [f32, f32, f32]
+            L.or_quantize30.restype = u32
+            L.or_split_words.argtypes = [u32, u32, u32, vp]
+            L.or_decode_words.argtypes = [u32, u32, u32, i32, vp]
+            L.or_morton_code.argtypes = [vp, vp, vp]
+            L.or_morton_code.restype = u64
+            L.or_num_batches.argtypes = [u64, u32]
+            L.or_num_batches.restype = u64
+            L.or_encode.argtypes = [vp, vp, u64, u32, vp, vp, vp, vp, vp, vp]
+            L.or_encode.restype = i32
+            L.or_project_position.argtypes = [vp, VP, u32, vp, vp, vp]
+            L.or_project_position.restype = i32
+            L.or_project_point.argtypes = [vp, i32, u32, u32, u32, u32, VP, vp, vp]
+            L.or_project_point.restype = i32
+            L.or_decode_position.argtypes = [vp, i32, u32, u32, u32, vp]
+            L.or_select_k.argtypes = [vp, VP]
+            L.or_select_k.restype = i32
+            L.or_cull.argtypes = [vp, VP]
+            L.or_cull.restype = i32
+            L.or_render.argtypes = [vp, u64, vp, vp, vp, VP, vp, vp, SP]
+            L.or_render_threaded.argtypes = [vp, u64, vp, vp, vp, VP, i32, vp, SP]
+            L.or_render_positions.argtypes = [vp, u64, VP, vp]
+            L.or_brute_force.argtypes = [vp, u64, vp, vp, vp, VP, vp]
+            L.or_resolve.argtypes = [vp, u64, vp, vp]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    assert a.flags.c_contiguous
+    return a.ctypes.data
+
+
+def make_view(m, width, height, cull=False, force_k=0, threshold_px=512.0) -> View:
+    v = View()
+    mm = np.asarray(m, np.float32).reshape(16)
+    for i in range(16):
+        v.m[i] = float(mm[i])
+    v.width, v.height = int(width), int(height)
+    v.cull, v.force_k, v.threshold_px = int(bool(cull)), int(force_k), float(threshold_px)
+    return v
+
+
+# ---- Eq. 1, Listing 2, Sec. 3.3 --------------------------------------------
+
+def quantize30(v, box_min, box_size) -> int:
+    return lib().or_quantize30(float(np.float32(v)), float(np.float32(box_min)),
+                               float(np.float32(box_size)))
+
+
+def split_words(X30, Y30, Z30):
+    w = np.zeros(3, np.uint32)
+    lib().or_split_words(int(X30), int(Y30), int(Z30), _p(w))
+    return [int(x) for x in w]
+
+
+def decode_words(w1, w2, w3, k):
+    out = np.zeros(3, np.uint32)
+    lib().or_decode_words(int(w1), int(w2), int(w3), int(k), _p(out))
+    return [int(x) for x in out]
+
+
+def morton_code(p, cmin, csize) -> int:
+    pp = np.asarray(p, np.float32).reshape(3).copy()
+    a = np.asarray(cmin, np.float64).reshape(3).copy()
+    b = np.asarray(csize, np.float64).reshape(3).copy()
+    return lib().or_morton_code(_p(pp), _p(a), _p(b))
+
+
+# ---- Sec. 3.1 encode ---------------------------------------------------------
+
+class Encoded:
+    """Oracle-encoded cloud: batches, the three coordinate words and colours in
+    Morton order, and perm (sorted position -> input index)."""
+
+    def __init__(self, batches, w1, w2, w3, color, perm):
+        self.batches, self.w1, self.w2, self.w3 = batches, w1, w2, w3
+        self.color, self.perm = color, perm
+
+    @property
+    def n(self):
+        return len(self.w1)
+
+
+def encode(xyz: np.ndarray, rgba: np.ndarray, batch_size: int = 10240) -> Encoded:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    rgba = np.ascontiguousarray(rgba, np.uint32)
+    n = len(rgba)
+    nb = lib().or_num_batches(n, batch_size)
+    batches = np.zeros(nb, BATCH_DTYPE)
+    w1 = np.zeros(n, np.uint32)
+    w2 = np.zeros(n, np.uint32)
+    w3 = np.zeros(n, np.uint32)
+    color = np.zeros(n, np.uint32)
+    perm = np.zeros(n, np.uint32)
+    rc = lib().or_encode(_p(xyz), _p(rgba), n, batch_size, _p(perm), _p(batches),
+                         _p(w1), _p(w2), _p(w3), _p(color))
+    if rc < 0:
+        raise RuntimeError(f"or_encode failed: {rc}")
+    return Encoded(batches, w1, w2, w3, color, perm)
+
+
+# ---- Listing 1 and the geometry pass -----------------------------------------
+
+def project_position(p, view: View, idx: int = 0):
+    """(accepted, pixel, key, fx, fy) for one float position."""
+    pp = np.asarray(p, np.float32).reshape(3).copy()
+    pix = np.zeros(1, np.uint32)
+    key = np.zeros(1, np.uint64)
+    fxy = np.zeros(2, np.float32)
+    ok = lib().or_project_position(_p(pp), ctypes.byref(view), idx, _p(pix), _p(key), _p(fxy))
+    return bool(ok), int(pix[0]), int(key[0]), float(fxy[0]), float(fxy[1])
+
+
+def _batch_arr(b):
+    a = np.zeros(1, BATCH_DTYPE)
+    a[0] = b
+    return a
+
+
+def decode_position(batch, k, w1, w2, w3):
+    b = _batch_arr(batch)
+    p = np.zeros(3, np.float32)
+    lib().or_decode_position(_p(b), int(k), int(w1), int(w2), int(w3), _p(p))
+    return p
+
+
+def select_k(batch, view: View) -> int:
+    return lib().or_select_k(_p(_batch_arr(batch)), ctypes.byref(view))
+
+
+def cull(batch, view: View) -> bool:
+    return bool(lib().or_cull(_p(_batch_arr(batch)), ctypes.byref(view)))
+
+
+def render(enc: Encoded, view: View, order=None):
+    """Visibility buffer (uint64[H*W]) and stats of one view."""
+    vis = np.empty(view.width * view.height, np.uint64)
+    st = Stats()
+    o = None
+    if order is not None:
+        o = np.ascontiguousarray(order, np.uint64)
+    lib().or_render(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2),
+                    _p(enc.w3), ctypes.byref(view), _p(o) if o is not None else None,
+                    _p(vis), ctypes.byref(st))
+    return vis, st.as_dict()
+
+
+def render_threaded(enc: Encoded, view: View, threads: int = 0):
+    vis = np.empty(view.width * view.height, np.uint64)
+    st = Stats()
+    lib().or_render_threaded(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2),
+                             _p(enc.w3), ctypes.byref(view),
+                             int(threads) if threads else (os.cpu_count() or 1),
+                             _p(vis), ctypes.byref(st))
+    return vis, st.as_dict()
+
+
+def render_positions(xyz: np.ndarray, view: View):
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    vis = np.empty(view.width * view.height, np.uint64)
+    lib().or_render_positions(_p(xyz), len(xyz), ctypes.byref(view), _p(vis))
+    return vis
+
+
+def brute_force(enc: Encoded, view: View):
+    vis = np.empty(view.width * view.height, np.uint64)
+    lib().or_brute_force(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2),
+                         _p(enc.w3), ctypes.byref(view), _p(vis))
+    return vis
+
+
+def resolve(vis: np.ndarray, color: np.ndarray):
+    vis = np.ascontiguousarray(vis, np.uint64)
+    color = np.ascontiguousarray(color, np.uint32)
+    out = np.empty(len(vis), np.uint32)
+    lib().or_resolve(_p(vis), len(vis), _p(color), _p(out))
+    return out

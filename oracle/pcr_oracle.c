@@ -1,0 +1,425 @@
+/* pcr_oracle.c — plain, slow CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * Restates, step by step and without any blocking, fusion or reordering, what
+ * the rasterizer of Schuetz, Kerbl and Wimmer (2022) computes:
+ *   Sec. 3.1   Morton order, batches of consecutive points, batch boxes;
+ *   Eq. 1      30-bit coordinates relative to the batch box;
+ *   Listing 2  three 10-bit-per-axis coordinate words;
+ *   Sec. 3.3   precision k chosen from the projected batch extent;
+ *   Sec. 3.2   batch frustum culling;
+ *   Listing 1  projection, 64-bit (depth bits << 32 | index) key, minimum;
+ *   Sec. 3.3   visibility buffer resolved to colours.
+ * Where the paper leaves the arithmetic open the readings are:
+ *   decode     x = min + float(Xk) * (size * 2^-10k), binary32;
+ *   project    c = ((m0 x + m4 y) + m8 z) + m12 per row, binary32, no FMA;
+ *   pixel      f = ((c / w) * 0.5 + 0.5) * W with an IEEE divide, accepted iff
+ *              w > 0 and 0 <= f < W, px = floor(f); row 0 at the bottom;
+ *   ties       the smaller key wins, so equal depths go to the smaller index;
+ *   precision  k = 1 if the extent of the 8 projected box corners is below
+ *              T = 512 px (0.5 px per cell of 1024), 2 if below 1024 T, else 3,
+ *              and 3 whenever a corner has w <= 0;
+ *   culling    conservative: a batch is dropped only when a rigorous rounding
+ *              bound proves every decoded point is rejected by one clip plane.
+ * Parity pins live in tests/test_oracle_*.py.
+ */
+#include "pcr_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- Eq. 1 and Listing 2 ------------------------------------------------- */
+
+uint32_t or_quantize30(float v, float box_min, float box_size) {
+    /* Eq. 1, evaluated in binary64 from the binary32 inputs; a zero-size box
+     * maps every point to 0; the result is clamped to 2^30 - 1 as printed. */
+    if (!(box_size > 0.0f)) return 0;
+    double t = floor(1073741824.0 * ((double)v - (double)box_min) / (double)box_size);
+    if (t < 0.0) t = 0.0;
+    if (t > 1073741823.0) t = 1073741823.0;
+    return (uint32_t)t;
+}
+
+void or_split_words(uint32_t X30, uint32_t Y30, uint32_t Z30, uint32_t w[3]) {
+    /* word 0 = low precision = bits 20..29, word 1 = medium = bits 10..19,
+     * word 2 = high = bits 0..9; each packs x | y << 10 | z << 20 */
+    for (int j = 0; j < 3; ++j) {
+        int shift = 20 - 10 * j;
+        uint32_t xs = (X30 >> shift) & 1023u;
+        uint32_t ys = (Y30 >> shift) & 1023u;
+        uint32_t zs = (Z30 >> shift) & 1023u;
+        w[j] = xs | (ys << 10) | (zs << 20);
+    }
+}
+
+void or_decode_words(uint32_t w1, uint32_t w2, uint32_t w3, int k, uint32_t out[3]) {
+    uint32_t words[3] = {w1, w2, w3};
+    for (int a = 0; a < 3; ++a) {
+        uint32_t v = 0;
+        for (int j = 0; j < k; ++j) v = (v << 10) | ((words[j] >> (10 * a)) & 1023u);
+        out[a] = v;
+    }
+}
+
+/* ---- Sec. 3.1: Morton order and batches ---------------------------------- */
+
+uint64_t or_morton_code(const float p[3], const double cmin[3], const double csize[3]) {
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        double t = 0.0;
+        if (csize[a] > 0.0) t = floor(2097152.0 * ((double)p[a] - cmin[a]) / csize[a]);
+        if (t < 0.0) t = 0.0;
+        if (t > 2097151.0) t = 2097151.0;
+        q[a] = (uint32_t)t;
+    }
+    uint64_t code = 0;
+    for (int bit = 0; bit < 21; ++bit)
+        for (int a = 0; a < 3; ++a)
+            code |= (uint64_t)((q[a] >> bit) & 1u) << (3 * bit + a);
+    return code;
+}
+
+uint64_t or_num_batches(uint64_t n, uint32_t batch_size) {
+    return batch_size ? (n + batch_size - 1) / batch_size : 0;
+}
+
+typedef struct { uint64_t code; uint32_t idx; } keyed;
+
+static int keyed_cmp(const void* a, const void* b) {
+    const keyed* x = (const keyed*)a;
+    const keyed* y = (const keyed*)b;
+    if (x->code != y->code) return x->code < y->code ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+int or_encode(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
+              uint32_t* perm, or_batch* batches, uint32_t* w1, uint32_t* w2,
+              uint32_t* w3, uint32_t* color) {
+    if (batch_size == 0 || n > 0xFFFFFFFFull) return -1;
+    if (n == 0) return 0;
+    /* cloud box */
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = xyz[a];
+    for (uint64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            float v = xyz[3 * i + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    double cmin[3], csize[3];
+    for (int a = 0; a < 3; ++a) {
+        cmin[a] = (double)lo[a];
+        csize[a] = (double)hi[a] - (double)lo[a];
+    }
+    /* stable sort by Morton code */
+    keyed* ks = (keyed*)malloc(sizeof(keyed) * n);
+    if (!ks) return -2;
+    for (uint64_t i = 0; i < n; ++i) {
+        ks[i].code = or_morton_code(&xyz[3 * i], cmin, csize);
+        ks[i].idx = (uint32_t)i;
+    }
+    qsort(ks, n, sizeof(keyed), keyed_cmp);
+    for (uint64_t j = 0; j < n; ++j) perm[j] = ks[j].idx;
+    free(ks);
+    /* batches of consecutive sorted points */
+    uint64_t nb = or_num_batches(n, batch_size);
+    for (uint64_t b = 0; b < nb; ++b) {
+        uint64_t first = b * batch_size;
+        uint64_t end = first + batch_size < n ? first + batch_size : n;
+        float bmin[3], bmax[3];
+        for (int a = 0; a < 3; ++a) bmin[a] = bmax[a] = xyz[3 * (uint64_t)perm[first] + a];
+        for (uint64_t j = first; j < end; ++j)
+            for (int a = 0; a < 3; ++a) {
+                float v = xyz[3 * (uint64_t)perm[j] + a];
+                if (v < bmin[a]) bmin[a] = v;
+                if (v > bmax[a]) bmax[a] = v;
+            }
+        or_batch* B = &batches[b];
+        for (int a = 0; a < 3; ++a) {
+            B->min[a] = bmin[a];
+            B->size[a] = bmax[a] - bmin[a];   /* binary32 subtraction */
+        }
+        B->first = (uint32_t)first;
+        B->count = (uint32_t)(end - first);
+        for (uint64_t j = first; j < end; ++j) {
+            const float* p = &xyz[3 * (uint64_t)perm[j]];
+            uint32_t X = or_quantize30(p[0], B->min[0], B->size[0]);
+            uint32_t Y = or_quantize30(p[1], B->min[1], B->size[1]);
+            uint32_t Z = or_quantize30(p[2], B->min[2], B->size[2]);
+            uint32_t w[3];
+            or_split_words(X, Y, Z, w);
+            w1[j] = w[0];
+            w2[j] = w[1];
+            w3[j] = w[2];
+            color[j] = rgba[perm[j]];
+        }
+    }
+    return (int)(nb > 0x7FFFFFFF ? 0x7FFFFFFF : nb);
+}
+
+/* ---- Sec. 3.3 decode and Listing 1 projection ---------------------------- */
+
+void or_decode_position(const or_batch* b, int k, uint32_t w1, uint32_t w2,
+                        uint32_t w3, float p[3]) {
+    uint32_t q[3];
+    or_decode_words(w1, w2, w3, k, q);
+    for (int a = 0; a < 3; ++a) {
+        float cell = ldexpf(b->size[a], -10 * k);   /* exact power-of-two scaling */
+        float fq = (float)q[a];                     /* exact for k <= 2, rounded for k = 3 */
+        float off = fq * cell;
+        p[a] = b->min[a] + off;
+    }
+}
+
+int or_project_position(const float p[3], const or_view* v, uint32_t idx,
+                        uint32_t* pixel, uint64_t* key, float fxy[2]) {
+    const float* m = v->m;
+    float x = p[0], y = p[1], z = p[2];
+    float cx = ((m[0] * x + m[4] * y) + m[8] * z) + m[12];
+    float cy = ((m[1] * x + m[5] * y) + m[9] * z) + m[13];
+    float cw = ((m[3] * x + m[7] * y) + m[11] * z) + m[15];
+    if (!(cw > 0.0f)) return 0;
+    float ndx = cx / cw;
+    float ndy = cy / cw;
+    float fx = (ndx * 0.5f + 0.5f) * (float)v->width;
+    float fy = (ndy * 0.5f + 0.5f) * (float)v->height;
+    if (fxy) { fxy[0] = fx; fxy[1] = fy; }
+    if (!(fx >= 0.0f && fx < (float)v->width)) return 0;
+    if (!(fy >= 0.0f && fy < (float)v->height)) return 0;
+    uint32_t px = (uint32_t)floorf(fx);
+    uint32_t py = (uint32_t)floorf(fy);
+    uint32_t bits;
+    memcpy(&bits, &cw, 4);
+    *pixel = py * v->width + px;
+    *key = ((uint64_t)bits << 32) | (uint64_t)idx;
+    return 1;
+}
+
+int or_project_point(const or_batch* b, int k, uint32_t w1, uint32_t w2, uint32_t w3,
+                     uint32_t idx, const or_view* v, uint32_t* pixel, uint64_t* key) {
+    float p[3];
+    or_decode_position(b, k, w1, w2, w3, p);
+    return or_project_position(p, v, idx, pixel, key, NULL);
+}
+
+/* ---- Sec. 3.3: precision from the projected extent ----------------------- */
+
+int or_select_k(const or_batch* b, const or_view* v) {
+    if (v->force_k >= 1 && v->force_k <= 3) return v->force_k;
+    float fmin[2] = {0, 0}, fmax[2] = {0, 0};
+    for (int c = 0; c < 8; ++c) {
+        float p[3];
+        for (int a = 0; a < 3; ++a)
+            p[a] = ((c >> a) & 1) ? b->min[a] + b->size[a] : b->min[a];
+        const float* m = v->m;
+        float cw = ((m[3] * p[0] + m[7] * p[1]) + m[11] * p[2]) + m[15];
+        if (!(cw > 0.0f)) return 3;
+        float f[2];
+        uint32_t pix;
+        uint64_t key;
+        or_project_position(p, v, 0, &pix, &key, f);
+        for (int a = 0; a < 2; ++a) {
+            if (c == 0 || f[a] < fmin[a]) fmin[a] = f[a];
+            if (c == 0 || f[a] > fmax[a]) fmax[a] = f[a];
+        }
+    }
+    float ex = fmax[0] - fmin[0];
+    float ey = fmax[1] - fmin[1];
+    float T = v->threshold_px;
+    if (ex < T && ey < T) return 1;
+    float T2 = T * 1024.0f;
+    if (ex < T2 && ey < T2) return 2;
+    return 3;
+}
+
+/* ---- Sec. 3.2: conservative batch frustum culling ------------------------ */
+
+/* Every decoded position lies in [min, fl(min + size)] per axis (rounding is
+ * monotonic and float(Xk) * cell <= size). For one matrix row r, the binary32
+ * value c computed by or_project_position differs from the exact r.(x,y,z,1)
+ * by at most gamma_4 * (|r0 x| + |r1 y| + |r2 z| + |r3|), gamma_4 = 4u/(1-4u),
+ * u = 2^-24 (dot-product error bound, Higham, Accuracy and Stability of
+ * Numerical Algorithms, 2nd ed., Sec. 3.1). The bound below uses 6u, which
+ * also covers the binary64 rounding of this test itself. */
+
+static double row_max(const double r[4], const double lo[3], const double hi[3]) {
+    double s = r[3];
+    for (int a = 0; a < 3; ++a) s += fmax(r[a] * lo[a], r[a] * hi[a]);
+    return s;
+}
+
+static double row_min(const double r[4], const double lo[3], const double hi[3]) {
+    double s = r[3];
+    for (int a = 0; a < 3; ++a) s += fmin(r[a] * lo[a], r[a] * hi[a]);
+    return s;
+}
+
+static double row_mag(const double r[4], const double lo[3], const double hi[3]) {
+    double s = fabs(r[3]);
+    for (int a = 0; a < 3; ++a) s += fabs(r[a]) * fmax(fabs(lo[a]), fabs(hi[a]));
+    return s;
+}
+
+int or_cull(const or_batch* b, const or_view* v) {
+    const double g = 6.0 * 0x1.0p-24;    /* rounding bound factor */
+    const double e1 = 1.0 + 0x1.0p-10;   /* clip-plane margin 1 + 2^-10 */
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (double)b->min[a];
+        hi[a] = (double)(float)(b->min[a] + b->size[a]);
+    }
+    const float* m = v->m;
+    double X[4] = {m[0], m[4], m[8], m[12]};
+    double Y[4] = {m[1], m[5], m[9], m[13]};
+    double Wr[4] = {m[3], m[7], m[11], m[15]};
+    double bx = row_mag(X, lo, hi), by = row_mag(Y, lo, hi), bw = row_mag(Wr, lo, hi);
+    if (!isfinite(bx) || !isfinite(by) || !isfinite(bw)) return 0;
+    /* every point has w <= 0 */
+    if (row_max(Wr, lo, hi) + g * bw <= 0.0) return 1;
+    double sp[4], sm[4];
+    /* x: left of -w and right of +w, each with margin 1 + 2^-10 */
+    for (int a = 0; a < 4; ++a) { sp[a] = X[a] + e1 * Wr[a]; sm[a] = X[a] - e1 * Wr[a]; }
+    double mx = g * (bx + e1 * bw);
+    if (row_max(sp, lo, hi) + mx < 0.0) return 1;
+    if (row_min(sm, lo, hi) - mx > 0.0) return 1;
+    for (int a = 0; a < 4; ++a) { sp[a] = Y[a] + e1 * Wr[a]; sm[a] = Y[a] - e1 * Wr[a]; }
+    double my = g * (by + e1 * bw);
+    if (row_max(sp, lo, hi) + my < 0.0) return 1;
+    if (row_min(sm, lo, hi) - my > 0.0) return 1;
+    return 0;
+}
+
+/* ---- geometry pass (Listing 1 over all batches) -------------------------- */
+
+static void render_range(const or_batch* batches, uint64_t lo, uint64_t hi,
+                         const uint64_t* order, const uint32_t* w1, const uint32_t* w2,
+                         const uint32_t* w3, const or_view* v, uint64_t* vis,
+                         or_stats* st) {
+    for (uint64_t t = lo; t < hi; ++t) {
+        const or_batch* b = &batches[order ? order[t] : t];
+        if (v->cull && or_cull(b, v)) continue;
+        int k = or_select_k(b, v);
+        if (st) {
+            st->batches_rendered += 1;
+            st->points_processed += b->count;
+            st->batches_k[k] += 1;
+            st->points_k[k] += b->count;
+        }
+        for (uint32_t j = 0; j < b->count; ++j) {
+            uint32_t i = b->first + j;
+            uint32_t pix;
+            uint64_t key;
+            if (!or_project_point(b, k, w1[i], w2[i], w3[i], i, v, &pix, &key)) continue;
+            if (st) st->points_accepted += 1;
+            if (key < vis[pix]) vis[pix] = key;
+        }
+    }
+}
+
+void or_render(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+               const uint32_t* w2, const uint32_t* w3, const or_view* v,
+               const uint64_t* order, uint64_t* vis, or_stats* st) {
+    uint64_t npix = (uint64_t)v->width * v->height;
+    for (uint64_t p = 0; p < npix; ++p) vis[p] = OR_EMPTY;
+    if (st) memset(st, 0, sizeof(*st));
+    render_range(batches, 0, nbatches, order, w1, w2, w3, v, vis, st);
+}
+
+typedef struct {
+    const or_batch* batches;
+    uint64_t lo, hi;
+    const uint32_t *w1, *w2, *w3;
+    const or_view* v;
+    uint64_t* vis;
+    or_stats st;
+} render_job;
+
+static void* render_thread(void* a) {
+    render_job* j = (render_job*)a;
+    uint64_t npix = (uint64_t)j->v->width * j->v->height;
+    for (uint64_t p = 0; p < npix; ++p) j->vis[p] = OR_EMPTY;
+    render_range(j->batches, j->lo, j->hi, NULL, j->w1, j->w2, j->w3, j->v, j->vis, &j->st);
+    return NULL;
+}
+
+void or_render_threaded(const or_batch* batches, uint64_t nbatches,
+                        const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                        const or_view* v, int threads, uint64_t* vis, or_stats* st) {
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    uint64_t npix = (uint64_t)v->width * v->height;
+    render_job* jobs = (render_job*)calloc((size_t)threads, sizeof(render_job));
+    pthread_t* tid = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    int* ok = (int*)calloc((size_t)threads, sizeof(int));
+    for (int t = 0; t < threads; ++t) {
+        render_job* j = &jobs[t];
+        j->batches = batches;
+        j->lo = nbatches * (uint64_t)t / (uint64_t)threads;
+        j->hi = nbatches * (uint64_t)(t + 1) / (uint64_t)threads;
+        j->w1 = w1; j->w2 = w2; j->w3 = w3; j->v = v;
+        j->vis = t == 0 ? vis : (uint64_t*)malloc(sizeof(uint64_t) * (npix ? npix : 1));
+        ok[t] = pthread_create(&tid[t], NULL, render_thread, j) == 0;
+        if (!ok[t]) render_thread(j);
+    }
+    if (st) memset(st, 0, sizeof(*st));
+    for (int t = 0; t < threads; ++t) {
+        if (ok[t]) pthread_join(tid[t], NULL);
+        if (t > 0) {
+            for (uint64_t p = 0; p < npix; ++p)
+                if (jobs[t].vis[p] < vis[p]) vis[p] = jobs[t].vis[p];
+            free(jobs[t].vis);
+        }
+        if (st) {
+            st->batches_rendered += jobs[t].st.batches_rendered;
+            st->points_processed += jobs[t].st.points_processed;
+            st->points_accepted += jobs[t].st.points_accepted;
+            for (int k = 0; k < 4; ++k) {
+                st->batches_k[k] += jobs[t].st.batches_k[k];
+                st->points_k[k] += jobs[t].st.points_k[k];
+            }
+        }
+    }
+    free(jobs);
+    free(tid);
+    free(ok);
+}
+
+void or_render_positions(const float* xyz, uint64_t n, const or_view* v, uint64_t* vis) {
+    uint64_t npix = (uint64_t)v->width * v->height;
+    for (uint64_t p = 0; p < npix; ++p) vis[p] = OR_EMPTY;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t pix;
+        uint64_t key;
+        if (or_project_position(&xyz[3 * i], v, (uint32_t)i, &pix, &key, NULL) &&
+            key < vis[pix])
+            vis[pix] = key;
+    }
+}
+
+void or_brute_force(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                    const uint32_t* w2, const uint32_t* w3, const or_view* v,
+                    uint64_t* vis) {
+    uint64_t npix = (uint64_t)v->width * v->height;
+    for (uint64_t p = 0; p < npix; ++p) {
+        uint64_t best = OR_EMPTY;
+        for (uint64_t b = 0; b < nbatches; ++b) {
+            int k = or_select_k(&batches[b], v);
+            for (uint32_t j = 0; j < batches[b].count; ++j) {
+                uint32_t i = batches[b].first + j;
+                uint32_t pix;
+                uint64_t key;
+                if (or_project_point(&batches[b], k, w1[i], w2[i], w3[i], i, v, &pix, &key) &&
+                    pix == p && key < best)
+                    best = key;
+            }
+        }
+        vis[p] = best;
+    }
+}
+
+void or_resolve(const uint64_t* vis, uint64_t npixels, const uint32_t* color,
+                uint32_t* out) {
+    for (uint64_t p = 0; p < npixels; ++p)
+        out[p] = vis[p] == OR_EMPTY ? 0u : color[(uint32_t)(vis[p] & 0xFFFFFFFFull)];
+}

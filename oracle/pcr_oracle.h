@@ -1,0 +1,126 @@
+/* pcr_oracle.h — plain, slow CPU oracle for one-pixel point rasterization of
+ * batched, adaptively quantized point clouds (Schuetz, Kerbl, Wimmer,
+ * "Software Rasterization of 2 Billion Points in Real Time", 2022).
+ *
+ * TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the CPU-baseline
+ * leg of the benchmark use it to check the GPU library; the library never
+ * calls it and shares no code with it.
+ *
+ * Compiled with -ffp-contract=off: every float operation below is one IEEE
+ * binary32 (or binary64 where stated) operation rounded to nearest, in the
+ * order written.
+ */
+#ifndef PCR_ORACLE_H
+#define PCR_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One batch (Sec. 3.1): bounding box (min corner and size, binary32), index of
+ * its first point in the encoded buffers and its number of points. */
+typedef struct {
+    float min[3];
+    float size[3];
+    uint32_t first;
+    uint32_t count;
+} or_batch;
+
+/* One camera view. m is the 4x4 world-to-clip matrix, column-major
+ * (clip = m * (x,y,z,1), element (row r, column c) at m[r + 4c]). */
+typedef struct {
+    float m[16];
+    uint32_t width, height;
+    int cull;            /* 1: batch frustum culling (Sec. 3.2) */
+    int force_k;         /* 0: adaptive precision (Sec. 3.3); 1..3: forced */
+    float threshold_px;  /* k = 1 if extent < T, 2 if extent < 1024 T, else 3 */
+} or_view;
+
+typedef struct {
+    uint64_t batches_rendered;   /* batches that passed culling */
+    uint64_t points_processed;   /* points of those batches */
+    uint64_t batches_k[4];       /* rendered batches per precision k */
+    uint64_t points_k[4];
+    uint64_t points_accepted;    /* points that landed inside the viewport */
+} or_stats;
+
+#define OR_EMPTY 0xFFFFFFFFFFFFFFFFull
+
+/* Eq. 1: 30-bit fixed-point coordinate relative to the batch box. */
+uint32_t or_quantize30(float v, float box_min, float box_size);
+
+/* Listing 2 and Sec. 3.3: split three 30-bit coordinates into the low (bits
+ * 20-29), medium (10-19) and high (0-9) precision words, each packing
+ * x | y << 10 | z << 20. */
+void or_split_words(uint32_t X30, uint32_t Y30, uint32_t Z30, uint32_t w[3]);
+
+/* Sec. 3.3: the k-word (10k-bit) integer coordinates of a point: the first k
+ * words concatenated from the most significant part down. out[a] < 2^(10k). */
+void or_decode_words(uint32_t w1, uint32_t w2, uint32_t w3, int k, uint32_t out[3]);
+
+/* Sec. 3.1: 63-bit Morton code (21 bits per axis, x in the lowest bit of each
+ * triple) of p over the cloud box (cmin, csize), computed in binary64. */
+uint64_t or_morton_code(const float p[3], const double cmin[3], const double csize[3]);
+
+/* Number of batches for n points and batch_size points per batch. */
+uint64_t or_num_batches(uint64_t n, uint32_t batch_size);
+
+/* Sec. 3.1 and 3.3: Morton-sort the cloud (stable: ties keep input order),
+ * cut it into batches of batch_size consecutive points, compute each batch's
+ * binary32 box and write the three coordinate words and the colour of every
+ * point in sorted order. perm[j] = input index of sorted point j. */
+int or_encode(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
+              uint32_t* perm, or_batch* batches, uint32_t* w1, uint32_t* w2,
+              uint32_t* w3, uint32_t* color);
+
+/* Listing 1: project one world position. Returns 1 and writes the pixel id
+ * (py * width + px) and the 64-bit key (bits of w_clip << 32 | idx) when the
+ * point lands in the viewport, else 0. When fxy is not NULL it receives the
+ * unfloored pixel coordinates. */
+int or_project_position(const float p[3], const or_view* v, uint32_t idx,
+                        uint32_t* pixel, uint64_t* key, float fxy[2]);
+
+/* Decode point idx of batch b at precision k (Sec. 3.3) and project it. */
+int or_project_point(const or_batch* b, int k, uint32_t w1, uint32_t w2, uint32_t w3,
+                     uint32_t idx, const or_view* v, uint32_t* pixel, uint64_t* key);
+
+/* The position a point decodes to at precision k (Sec. 3.3). */
+void or_decode_position(const or_batch* b, int k, uint32_t w1, uint32_t w2,
+                        uint32_t w3, float p[3]);
+
+/* Sec. 3.3: precision of a batch in a view, from its projected extent. */
+int or_select_k(const or_batch* b, const or_view* v);
+
+/* Sec. 3.2: 1 if no point of the batch can land in the viewport. */
+int or_cull(const or_batch* b, const or_view* v);
+
+/* Sec. 3.2-3.3 geometry pass: vis[W*H] <- min key per pixel. vis is cleared
+ * first. order (may be NULL) lists the batch indices in processing order. */
+void or_render(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+               const uint32_t* w2, const uint32_t* w3, const or_view* v,
+               const uint64_t* order, uint64_t* vis, or_stats* st);
+
+/* The same on `threads` threads, each with a private visibility buffer that
+ * is merged by element-wise minimum. */
+void or_render_threaded(const or_batch* batches, uint64_t nbatches,
+                        const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                        const or_view* v, int threads, uint64_t* vis, or_stats* st);
+
+/* Unquantized image: every float position projected directly, key index = i. */
+void or_render_positions(const float* xyz, uint64_t n, const or_view* v, uint64_t* vis);
+
+/* Brute force: for every pixel, search every point of every batch for the
+ * smallest key that lands on that pixel (no culling). O(pixels * points). */
+void or_brute_force(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                    const uint32_t* w2, const uint32_t* w3, const or_view* v,
+                    uint64_t* vis);
+
+/* Sec. 3.3 visibility buffer: out[p] = colour of the winning point, 0 where
+ * no point landed. */
+void or_resolve(const uint64_t* vis, uint64_t npixels, const uint32_t* color,
+                uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,70 @@
+"""Planted-mistake check of the oracle pins.
+
+Each case copies oracle/pcr_oracle.c into a temporary directory, plants one
+plausible mistake (a dropped term, a wrong sign, shift or index, a transposed
+operand, a wrong tie-break), builds the copy and runs tests/test_oracle_pins.py
+against it. Every planted mistake must make at least one pin fail. The oracle
+in the tree is never modified.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pcr_oracle.c")
+
+# (name, text in pcr_oracle.c, replacement); the first occurrence is replaced
+MUTANTS = [
+    ("eq1_no_min", "((double)v - (double)box_min)", "((double)v)"),
+    ("eq1_scale", "floor(1073741824.0 *", "floor(2147483648.0 *"),
+    ("words_reversed", "int shift = 20 - 10 * j;", "int shift = 10 * j;"),
+    ("words_yz_swapped", "xs | (ys << 10) | (zs << 20)", "xs | (zs << 10) | (ys << 20)"),
+    ("decode_shift", "v = (v << 10) |", "v = (v << 9) |"),
+    ("morton_axis_order", "<< (3 * bit + a)", "<< (3 * bit + 2 - a)"),
+    ("sort_unstable", "return x->idx < y->idx ? -1 : (x->idx > y->idx);",
+     "return x->idx > y->idx ? -1 : (x->idx < y->idx);"),
+    ("box_size_is_max", "B->size[a] = bmax[a] - bmin[a];", "B->size[a] = bmax[a];"),
+    ("decode_no_min", "p[a] = b->min[a] + off;", "p[a] = off;"),
+    ("decode_cell", "ldexpf(b->size[a], -10 * k)", "ldexpf(b->size[a], -10)"),
+    ("project_transposed", "float cx = ((m[0] * x + m[4] * y) + m[8] * z) + m[12];",
+     "float cx = ((m[0] * x + m[1] * y) + m[2] * z) + m[3];"),
+    ("project_w_row", "float cw = ((m[3] * x + m[7] * y) + m[11] * z) + m[15];\n    if (!(cw > 0.0f)) return 0;",
+     "float cw = ((m[2] * x + m[6] * y) + m[10] * z) + m[14];\n    if (!(cw > 0.0f)) return 0;"),
+    ("pixel_no_offset", "(ndx * 0.5f + 0.5f)", "(ndx * 0.5f)"),
+    ("pixel_y_flip", "(ndy * 0.5f + 0.5f)", "(0.5f - ndy * 0.5f)"),
+    ("key_depth_from_x", "memcpy(&bits, &cw, 4);", "memcpy(&bits, &cx, 4);"),
+    ("no_min_update", "if (key < vis[pix]) vis[pix] = key;", "vis[pix] = key;"),
+    ("k_any_axis", "if (ex < T && ey < T) return 1;", "if (ex < T || ey < T) return 1;"),
+    ("k2_threshold", "float T2 = T * 1024.0f;", "float T2 = T * 1000.0f;"),
+    ("cull_any_corner", "if (row_max(sp, lo, hi) + mx < 0.0) return 1;",
+     "if (row_min(sp, lo, hi) + mx < 0.0) return 1;"),
+    ("cull_behind_any", "if (row_max(Wr, lo, hi) + g * bw <= 0.0) return 1;",
+     "if (row_min(Wr, lo, hi) + g * bw <= 0.0) return 1;"),
+    ("resolve_index", "color[(uint32_t)(vis[p] & 0xFFFFFFFFull)]", "color[(uint32_t)(vis[p] >> 32) & 3u]"),
+    ("merge_max", "if (jobs[t].vis[p] < vis[p]) vis[p] = jobs[t].vis[p];",
+     "if (jobs[t].vis[p] > vis[p] && jobs[t].vis[p] != OR_EMPTY) vis[p] = jobs[t].vis[p];"),
+    ("index_not_global", "uint32_t i = b->first + j;\n            uint32_t pix;",
+     "uint32_t i = j;\n            uint32_t pix;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(tmp_path, name, old, new):
+    with open(SRC) as f:
+        src = f.read()
+    assert old in src, f"mutation site for {name} not found"
+    mutated = src.replace(old, new, 1)
+    cfile = tmp_path / "pcr_oracle.c"
+    cfile.write_text(mutated)
+    hdr = os.path.join(ROOT, "oracle", "pcr_oracle.h")
+    (tmp_path / "pcr_oracle.h").write_text(open(hdr).read())
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread",
+                           "-ffp-contract=off", "-o", str(so), str(cfile), "-lm"])
+    env = dict(os.environ, PCR_ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
