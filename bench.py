@@ -1,0 +1,323 @@
+"""Benchmark: one-pixel point rasterization of a 2-billion-point cloud.
+
+A step is one frame of the whole hot path through the library: clear, batch
+culling and precision selection, raster into the 64-bit visibility buffer,
+resolve. Workload: 2,000,000,000 synthetic terrain points over 40 km x 40 km
+with 20 % on box buildings (seeded), Morton-sorted batches of 10,240 with
+three 10-bit words per point, one 1920x1080 overview frame that sees the
+whole cloud. The cloud (32 GB) is far larger than L2, so nothing stays cached
+between frames.
+
+value      processed points per second over K frames (CUDA events on the
+           rendering stream, inputs resident in HBM)
+e2e        the same metric through pc_render_host: the RGBA image of every
+           frame copied to pinned host memory, timed on the host
+roofline   the raster kernel: algorithmic bytes (coordinate words of the
+           processed batches at their precision + 32 B batch records) over
+           its mean CUDA-event duration, against the measured HBM copy peak
+cpu_baseline  the CPU oracle, threaded over the host cores, on a sample of
+           the same cloud and camera
+
+--impl reference times the CPU oracle alone (the paper's method restated on
+the CPU) as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpoints/s & ms/frame at 2B pts 1080p; %HBM peak; batched views/s, p50/p99"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--points", type=float, default=2e9)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=float, default=8e6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--verbose", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    import pcsynth
+    extent = 40000.0
+    params = pcsynth.terrain_params(extent, 0.2, 20000)
+    m = pcsynth.overview(params, args.width, args.height)
+    name = (f"{int(args.points):,} terrain+buildings points (40 km, seed {args.seed}), "
+            f"{args.width}x{args.height} overview frame, batches of 10,240")
+    return params, m, name
+
+
+def log(args, *a):
+    if args.verbose:
+        print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_baseline(args, params, m, sample_points, threads=None):
+    """The CPU oracle on the first `sample_points` points of the same seeded
+    cloud (each point is an independent draw, so this is a uniform sample),
+    same camera; returns (points/s, cores, description, encoded, view)."""
+    import oracle
+    import pcsynth
+    n = int(sample_points)
+    xyz, rgba = pcsynth.terrain(n, params, seed=args.seed)
+    enc = oracle.encode(xyz, rgba, 10240)
+    v = oracle.make_view(m, args.width, args.height, cull=True)
+    cores = threads or os.cpu_count() or 1
+    oracle.render_threaded(enc, v, threads=cores)         # warm-up
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        _, st = oracle.render_threaded(enc, v, threads=cores)
+        reps += 1
+        if time.perf_counter() - t0 > 3.0 and reps >= 2:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    pps = st["points_processed"] / dt
+    desc = (f"oracle geometry pass + culling, threaded on {cores} host cores, over the first "
+            f"{n:,} points of the same cloud ({st['points_processed']:,} processed), "
+            f"same camera, {reps} repetitions")
+    return pps, cores, desc, enc, v
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    params, m, name = workload(args)
+    import oracle
+    pps, cores, desc, enc, v = cpu_baseline(args, params, m, args.cpu_sample)
+    for _ in range(args.warmup):
+        oracle.render_threaded(enc, v, threads=cores)
+    t0 = time.perf_counter()
+    processed = 0
+    for _ in range(args.steps):
+        _, st = oracle.render_threaded(enc, v, threads=cores)
+        processed += st["points_processed"]
+    dt = time.perf_counter() - t0
+    value = processed / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpoints/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "sample_points": int(args.cpu_sample),
+                       "width": args.width, "height": args.height, "oracle": "CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": "Gpoints/s", "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "Gpoints/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2204_01287_gb300 as pcr
+    import pcsynth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        # replicas: every rank renders the same workload on its own GPU
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    pcr.build()
+
+    params, m, name = workload(args)
+    n = int(args.points)
+    t0 = time.perf_counter()
+    xyz = np.empty((n, 3), np.float32)
+    rgba = np.empty(n, np.uint32)
+    pcsynth.terrain(n, params, seed=args.seed, out=(xyz, rgba))
+    t_gen = time.perf_counter() - t0
+    log(args, f"generated {n:,} points in {t_gen:.1f}s")
+    ctx = pcr.Context(local)
+    t0 = time.perf_counter()
+    cloud = ctx.upload(xyz, rgba)
+    t_up = time.perf_counter() - t0
+    log(args, f"encoded + uploaded in {t_up:.1f}s")
+    del xyz, rgba
+
+    W, H = args.width, args.height
+    view = pcr.make_view(m, W, H, pcr.PC_VIEW_CULL)
+    fbs = ctx.framebuffers([view])
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        ctx.render(cloud, [view], fbs)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    points_per_frame = st["points_processed"]
+    raster_bytes = st["words_loaded_bytes"] + 32 * st["batches_rendered"]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    pcr.pc_timing_begin(ctx.h)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.render(cloud, [view], fbs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    timing = pcr.pc_timing_end(ctx.h)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_frame = ms / args.steps
+    value = points_per_frame * args.steps * world / (ms / 1e3) / 1e9
+
+    raster_ms = timing.ms_raster / max(1, timing.frames)
+    peak, peak_kind = peaks()
+    achieved = raster_bytes / (raster_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_raster", "kernel_ms": raster_ms,
+                "algorithmic_bytes": raster_bytes, "peak_source": peak_kind}
+    frame_bytes = raster_bytes + 16 * W * H + 4 * W * H
+    passes = {"clear_ms": timing.ms_clear / max(1, timing.frames),
+              "cull_ms": timing.ms_cull / max(1, timing.frames),
+              "raster_ms": raster_ms,
+              "resolve_ms": timing.ms_resolve / max(1, timing.frames),
+              "frame_hbm_frac": frame_bytes / (ms_per_frame / 1e3) / 1e9 / peak}
+
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(W * H, dtype=torch.int32, pin_memory=True)
+        hv = host.numpy().view(np.uint32)
+        for _ in range(3):
+            pcr.pc_render_host(ctx.h, cloud, [view], [hv], stream.cuda_stream)
+        k2 = max(20, args.steps // 4)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            pcr.pc_render_host(ctx.h, cloud, [view], [hv], stream.cuda_stream)
+        dt = time.perf_counter() - t0
+        e2e = {"value": points_per_frame * k2 * world / dt / 1e9, "unit": "Gpoints/s",
+               "h2d_bytes_per_step": int(np.dtype(np.uint8).itemsize * 80),
+               "d2h_bytes_per_step": W * H * 4, "steps": k2,
+               "ms_per_step": dt / k2 * 1e3, "api": "pc_render_host"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pps, cores, desc, _, _ = cpu_baseline(args, params, m, args.cpu_sample)
+        cpu = {"value": pps / 1e9, "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_frame,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": name, "points": n, "width": W, "height": H,
+                           "points_processed_per_frame": points_per_frame,
+                           "batches_rendered": st["batches_rendered"],
+                           "batches_k": st["batches_k"][1:],
+                           "l2": "inputs larger than L2 (32 GB cloud vs 129 MB L2)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "setup_s": {"generate": t_gen, "encode_upload": t_up}},
+                "roofline": roofline, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(timing.launches), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,262 @@
+/* pc.h — C ABI of the GB300 point-cloud rasterizer (libpcr.so).
+ *
+ * One-pixel point rasterization of large coloured point clouds after Schuetz,
+ * Kerbl and Wimmer, "Software Rasterization of 2 Billion Points in Real Time"
+ * (2022): points are Morton-sorted and cut into batches (Sec. 3.1), each batch
+ * stores its coordinates as three 10-bit-per-axis words relative to its box
+ * (Eq. 1, Listing 2), and every frame culls batches (Sec. 3.2), picks 10, 20
+ * or 30 bits per batch from its projected size (Sec. 3.3), writes
+ * (depth bits << 32 | point index) into a 64-bit visibility buffer with
+ * atomicMin (Listing 1) and resolves the winners' colours (Sec. 3.3).
+ *
+ * Conventions
+ *  - Every entry point returns a pc_status (PC_OK = 0, errors < 0); no C++
+ *    exception crosses this boundary. pc_last_error() gives the message of the
+ *    last failure on a context.
+ *  - Sizes are 64-bit. A cloud holds at most 2^32 - 1 points (the point index
+ *    is the low 32 bits of a visibility-buffer key).
+ *  - "host" pointers are ordinary CPU memory (pinned or pageable); "device"
+ *    pointers are CUDA global memory on the context's device (for example the
+ *    data_ptr() of a torch CUDA tensor). Streams are cudaStream_t values passed
+ *    as void*; NULL is the legacy default stream.
+ *  - Device work never traps and never waits without a bound: anomalies set a
+ *    device error flag that the next synchronizing call reports as PC_EDEVICE.
+ *  - Matrices are 4x4 float, column-major: clip = M * (x, y, z, 1), element
+ *    (row r, column c) at view_proj[r + 4c]; w_clip > 0 in front of the camera.
+ *  - Pixel (px, py) of a width x height view is element py * width + px, row 0
+ *    at the bottom (ndc y = -1).
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pc_status;
+#define PC_OK         0
+#define PC_EINVAL    -1   /* bad argument (null pointer, size out of range) */
+#define PC_ENOMEM    -2   /* host or device allocation failed */
+#define PC_ENOTFOUND -3   /* unknown cloud handle or ticket */
+#define PC_EBUSY     -4   /* admission refused: no view slot or framebuffer memory */
+#define PC_ETIMEDOUT -5   /* pc_poll: the request did not finish in time */
+#define PC_ECUDA     -6   /* a CUDA runtime call failed */
+#define PC_ENOTSUP   -7   /* operation not supported for this cloud or device */
+#define PC_EDEVICE   -8   /* a kernel raised its error flag (see pc_last_error) */
+
+typedef struct pc_ctx pc_ctx;
+typedef uint64_t pc_cloud;    /* 0 is never a valid handle */
+typedef uint64_t pc_ticket;   /* 0 is never a valid ticket */
+
+/* ---- configuration ------------------------------------------------------ */
+
+#define PC_CFG_TIMING 1u      /* record per-pass CUDA events in pc_render */
+
+typedef struct {
+    uint32_t batch_size;          /* points per batch, multiple of 4 (default 10240, Sec. 3.1) */
+    float    precision_px;        /* T: k = 1 if the projected batch extent < T px,
+                                     2 if < 1024 T, else 3 (default 512 = 0.5 px per cell
+                                     of 1024; the paper's 500 is selectable, Sec. 3.3) */
+    uint32_t encoder_threads;     /* host encoder threads, 0 = all cores */
+    uint32_t flags;               /* PC_CFG_* */
+    uint64_t serve_pool_bytes;    /* device memory for library-owned serving framebuffers
+                                     (default 2 GiB) */
+    uint32_t serve_streams;       /* CUDA streams of the serving loop (default 4) */
+    uint32_t max_views_per_launch;/* views rendered by one raster launch, 1..32 (default 32) */
+    uint32_t threads_per_block;   /* raster launch shape; 0 = autotuned */
+    uint32_t blocks_per_sm;       /* raster launch shape; 0 = autotuned */
+    uint32_t reserved[4];
+} pc_config;
+
+/* Fill cfg with the defaults listed above. */
+void pc_config_default(pc_config* cfg);
+
+/* ---- data layout (Sec. 3.1, Fig. "batches", Listing 2) ------------------- */
+
+/* One batch: binary32 box (min corner, size = max - min), index of the first
+ * point in the encoded buffers and number of points. 32 bytes. */
+typedef struct {
+    float    min[3];
+    float    size[3];
+    uint32_t first;
+    uint32_t count;
+} pc_batch;
+
+/* ---- contexts ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (cfg may be NULL for defaults).
+ * Allocates the context's scratch memory. *out receives the context. */
+pc_status pc_create(pc_ctx** out, int device, const pc_config* cfg);
+
+/* Release every cloud, ticket and buffer of the context (waits for its work). */
+void pc_destroy(pc_ctx* ctx);
+
+/* Static text for a status code. */
+const char* pc_strerror(pc_status s);
+
+/* Message of the last failure on ctx (empty string if none). Owned by ctx. */
+const char* pc_last_error(pc_ctx* ctx);
+
+/* ---- encoding and upload (Sec. 3.1, Eq. 1, Listing 2) -------------------- */
+
+/* Host encoder, alone (no GPU needed). Sorts the n points of xyz (host, n*3
+ * floats, x y z per point) by 63-bit Morton code over the cloud's box (21 bits
+ * per axis, binary64, ties keep input order), cuts them into batches of
+ * batch_size consecutive points, computes each batch's binary32 box and writes
+ * Eq. 1's 30-bit coordinates split into three words per point. Outputs (host,
+ * caller-allocated): batches[ceil(n / batch_size)], w1/w2/w3/color[n] in sorted
+ * order, perm[n] (sorted position -> input index; may be NULL). rgba may be NULL
+ * (colour 0). threads = 0 uses all cores. PC_EINVAL if n >= 2^32 or batch_size
+ * is 0 or not a multiple of 4. */
+pc_status pc_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
+                    uint32_t batch_size, uint32_t threads, pc_batch* batches,
+                    uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color,
+                    uint32_t* perm);
+
+/* Encode host points (as pc_encode, batch size from the context's config) and
+ * upload the cloud to device memory owned by the library. Synchronous. xyz and
+ * rgba are read only during the call. *out receives a cloud handle. */
+pc_status pc_upload_cloud(pc_ctx* ctx, const float* xyz, const uint32_t* rgba,
+                          uint64_t n, pc_cloud* out);
+
+/* Upload an already encoded cloud (host buffers in the pc_encode layout; the
+ * library copies them). Every batch must satisfy first + count <= n. */
+pc_status pc_upload_encoded(pc_ctx* ctx, const pc_batch* batches, uint64_t nbatches,
+                            const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                            const uint32_t* color, uint64_t n, pc_cloud* out);
+
+typedef struct {
+    uint64_t n_points;
+    uint64_t n_batches;
+    uint64_t device_bytes;   /* device memory held by the cloud */
+    uint32_t is_lod;         /* 1 for a cloud made by pc_build_lod */
+    uint32_t lod_levels;
+} pc_cloud_info;
+
+pc_status pc_cloud_get_info(pc_ctx* ctx, pc_cloud cloud, pc_cloud_info* info);
+
+/* Copy a cloud's device buffers back to host arrays sized as in pc_encode
+ * (any pointer may be NULL to skip it). Synchronous. */
+pc_status pc_cloud_download(pc_ctx* ctx, pc_cloud cloud, pc_batch* batches,
+                            uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color);
+
+/* Free a cloud's device memory (waits for work that uses it). */
+pc_status pc_release_cloud(pc_ctx* ctx, pc_cloud cloud);
+
+/* ---- level of detail (Sec. 3.5) ------------------------------------------ */
+
+typedef struct {
+    uint32_t max_levels;      /* octree depth limit (default 12) */
+    uint32_t max_node_points; /* points per node (default 10240) */
+    uint32_t seed;            /* subsampling seed */
+    uint32_t reserved;
+} pc_lod_opts;
+
+/* Build a layered octree (Sec. 3.5) from a cloud uploaded with pc_upload_cloud:
+ * each node is a batch of <= max_node_points points on a cubic box, parents
+ * hold uniform subsets of their children's points (additive LOD). Views with
+ * lod_px > 0 render only nodes whose projected extent is >= lod_px and whose
+ * parent is rendered. *out receives a new cloud; src stays valid. */
+pc_status pc_build_lod(pc_ctx* ctx, pc_cloud src, const pc_lod_opts* opts, pc_cloud* out);
+
+/* ---- rendering (Sec. 3.2-3.3, Sec. 3.7) ---------------------------------- */
+
+#define PC_VIEW_CULL           1u          /* batch frustum culling (Sec. 3.2) */
+#define PC_VIEW_NO_EARLY_DEPTH 2u          /* skip the non-atomic depth pre-test */
+#define PC_VIEW_FORCE_K(k)     (((uint32_t)(k) & 3u) << 4)  /* 1..3: fixed precision */
+#define PC_VIEW_K_MASK         0x30u
+
+typedef struct {
+    float    view_proj[16];   /* world -> clip, column-major */
+    uint32_t width, height;   /* 1..16384 */
+    uint32_t flags;           /* PC_VIEW_* */
+    float    lod_px;          /* LOD clouds: node threshold in px (Sec. 3.5); 0 = all nodes */
+} pc_view;
+
+/* Caller-owned device framebuffer of one view: vis[width*height] (uint64 keys)
+ * and rgba[width*height] (R | G<<8 | B<<16 | A<<24, 0 where no point landed).
+ * rgba may be NULL to skip the resolve. Both 16-byte aligned. */
+typedef struct {
+    uint64_t* vis;
+    uint32_t* rgba;
+} pc_framebuffer;
+
+/* Render nviews (1..256) views of a cloud, stream-ordered and asynchronous:
+ * per view, clear vis to all ones, cull and choose precision per batch, raster
+ * every point of the surviving batches into vis with atomicMin on
+ * (bits(w_clip) << 32 | index), then resolve rgba. Views are rendered by
+ * multi-view launches of up to max_views_per_launch views that read each
+ * batch's coordinate words once (Sec. 3.7). The result is bit-identical to
+ * rendering each view alone. Calls sharing a context may use different
+ * streams; each stream gets its own scratch. */
+pc_status pc_render(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
+                    const pc_framebuffer* fbs, void* stream);
+
+/* End-to-end variant: renders into library-owned device framebuffers and
+ * copies each view's RGBA image into host_rgba[v] (host, width*height
+ * uint32). Returns when the host images are complete. */
+pc_status pc_render_host(pc_ctx* ctx, pc_cloud cloud, const pc_view* views,
+                         uint32_t nviews, uint32_t* const* host_rgba, void* stream);
+
+/* Per-view counters of the last pc_render on `stream` of this context
+ * (synchronizes that stream). Mirrors Table 2's processed nodes and points. */
+typedef struct {
+    uint64_t batches_total;
+    uint64_t batches_rendered;     /* passed culling (and LOD selection) */
+    uint64_t batches_k[4];         /* rendered batches per precision k (index 1..3) */
+    uint64_t points_k[4];          /* their points */
+    uint64_t points_processed;     /* sum of points_k */
+    uint64_t words_loaded_bytes;   /* coordinate bytes the raster launch loaded for this view */
+} pc_view_stats;
+
+pc_status pc_get_view_stats(pc_ctx* ctx, void* stream, uint32_t view, pc_view_stats* out);
+
+/* ---- timing (per-pass CUDA events) --------------------------------------- */
+
+typedef struct {
+    uint32_t frames;            /* pc_render calls recorded */
+    uint32_t launches;          /* kernels launched by those calls */
+    double   ms_clear, ms_cull, ms_raster, ms_resolve;  /* summed over frames */
+    uint64_t raster_launches;
+} pc_timing;
+
+/* Start recording per-pass events for pc_render on this context (needs
+ * PC_CFG_TIMING or enables it), discarding earlier records. */
+pc_status pc_timing_begin(pc_ctx* ctx);
+/* Synchronize the recorded events and sum them. */
+pc_status pc_timing_end(pc_ctx* ctx, pc_timing* out);
+
+/* ---- serving loop ---------------------------------------------------------- */
+
+typedef struct {
+    pc_status status;         /* PC_OK or the failure of this request */
+    uint32_t  nviews;
+    uint32_t* const* rgba;    /* host images, one per view, owned by the context
+                                 until pc_release_ticket */
+    const uint32_t* widths;
+    const uint32_t* heights;
+    double    t_submit_ms, t_start_ms, t_done_ms;   /* steady clock, ms since ctx creation */
+} pc_result;
+
+/* Queue a request: nviews (1..32) views of a resident cloud. The library owns
+ * the framebuffers (admitted when serve_pool_bytes has room and a view slot
+ * is free) and returns host RGBA images through pc_poll. Requests that arrive
+ * while others run join the next launch group of the same cloud. Returns
+ * PC_EBUSY when the request can never fit the pool. */
+pc_status pc_submit(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
+                    pc_ticket* out);
+
+/* Wait up to timeout_ms (0 = just test, < 0 = no limit) for a request.
+ * PC_ETIMEDOUT if it has not finished; on PC_OK *out describes the result. */
+pc_status pc_poll(pc_ctx* ctx, pc_ticket ticket, int32_t timeout_ms, pc_result* out);
+
+/* Free a finished request's host images. */
+pc_status pc_release_ticket(pc_ctx* ctx, pc_ticket ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC_H */

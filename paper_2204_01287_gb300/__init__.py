@@ -1,0 +1,388 @@
+"""Python binding of libpcr.so, the GB300 point-cloud rasterizer.
+
+Thin ctypes marshalling over the C ABI in include/pc.h; the functions keep the
+C names (pc_create, pc_upload_cloud, pc_render, ...). Every step of a frame runs
+in the library's CUDA kernels; PyTorch only supplies device memory (tensors)
+and streams. There is no CPU fallback: if libpcr.so is missing or fails to
+load, importing the binding raises.
+
+Convenience layer: :class:`Context` wraps a pc_ctx with numpy/torch helpers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build_mod
+
+_lib = None
+_lock = threading.Lock()
+
+PC_OK, PC_EINVAL, PC_ENOMEM, PC_ENOTFOUND = 0, -1, -2, -3
+PC_EBUSY, PC_ETIMEDOUT, PC_ECUDA, PC_ENOTSUP, PC_EDEVICE = -4, -5, -6, -7, -8
+PC_CFG_TIMING = 1
+PC_VIEW_CULL = 1
+PC_VIEW_NO_EARLY_DEPTH = 2
+EMPTY = 0xFFFFFFFFFFFFFFFF
+
+
+def PC_VIEW_FORCE_K(k: int) -> int:
+    return (int(k) & 3) << 4
+
+
+BATCH_DTYPE = np.dtype([("min", "<f4", (3,)), ("size", "<f4", (3,)),
+                        ("first", "<u4"), ("count", "<u4")])
+
+
+class pc_config(ctypes.Structure):
+    _fields_ = [("batch_size", ctypes.c_uint32), ("precision_px", ctypes.c_float),
+                ("encoder_threads", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("serve_pool_bytes", ctypes.c_uint64), ("serve_streams", ctypes.c_uint32),
+                ("max_views_per_launch", ctypes.c_uint32),
+                ("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
+
+
+class pc_view(ctypes.Structure):
+    _fields_ = [("view_proj", ctypes.c_float * 16), ("width", ctypes.c_uint32),
+                ("height", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("lod_px", ctypes.c_float)]
+
+
+class pc_framebuffer(ctypes.Structure):
+    _fields_ = [("vis", ctypes.c_void_p), ("rgba", ctypes.c_void_p)]
+
+
+class pc_cloud_info(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_uint64), ("n_batches", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("is_lod", ctypes.c_uint32),
+                ("lod_levels", ctypes.c_uint32)]
+
+
+class pc_view_stats(ctypes.Structure):
+    _fields_ = [("batches_total", ctypes.c_uint64), ("batches_rendered", ctypes.c_uint64),
+                ("batches_k", ctypes.c_uint64 * 4), ("points_k", ctypes.c_uint64 * 4),
+                ("points_processed", ctypes.c_uint64),
+                ("words_loaded_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {"batches_total": self.batches_total, "batches_rendered": self.batches_rendered,
+                "batches_k": list(self.batches_k), "points_k": list(self.points_k),
+                "points_processed": self.points_processed,
+                "words_loaded_bytes": self.words_loaded_bytes}
+
+
+class pc_timing(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_uint32), ("launches", ctypes.c_uint32),
+                ("ms_clear", ctypes.c_double), ("ms_cull", ctypes.c_double),
+                ("ms_raster", ctypes.c_double), ("ms_resolve", ctypes.c_double),
+                ("raster_launches", ctypes.c_uint64)]
+
+
+class pc_lod_opts(ctypes.Structure):
+    _fields_ = [("max_levels", ctypes.c_uint32), ("max_node_points", ctypes.c_uint32),
+                ("seed", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class pc_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("nviews", ctypes.c_uint32),
+                ("rgba", ctypes.POINTER(ctypes.POINTER(ctypes.c_uint32))),
+                ("widths", ctypes.POINTER(ctypes.c_uint32)),
+                ("heights", ctypes.POINTER(ctypes.c_uint32)),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/pc.h
+_vp, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+_P = ctypes.POINTER
+SIGNATURES = [
+    ("pc_config_default", None, [_P(pc_config)]),
+    ("pc_strerror", ctypes.c_char_p, [_i32]),
+    ("pc_create", _i32, [_P(_vp), ctypes.c_int, _P(pc_config)]),
+    ("pc_destroy", None, [_vp]),
+    ("pc_last_error", ctypes.c_char_p, [_vp]),
+    ("pc_encode", _i32, [_vp, _vp, _u64, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("pc_upload_cloud", _i32, [_vp, _vp, _vp, _u64, _P(_u64)]),
+    ("pc_upload_encoded", _i32, [_vp, _vp, _u64, _vp, _vp, _vp, _vp, _u64, _P(_u64)]),
+    ("pc_cloud_get_info", _i32, [_vp, _u64, _P(pc_cloud_info)]),
+    ("pc_cloud_download", _i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
+    ("pc_release_cloud", _i32, [_vp, _u64]),
+    ("pc_build_lod", _i32, [_vp, _u64, _P(pc_lod_opts), _P(_u64)]),
+    ("pc_render", _i32, [_vp, _u64, _P(pc_view), _u32, _P(pc_framebuffer), _vp]),
+    ("pc_render_host", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_vp), _vp]),
+    ("pc_get_view_stats", _i32, [_vp, _vp, _u32, _P(pc_view_stats)]),
+    ("pc_timing_begin", _i32, [_vp]),
+    ("pc_timing_end", _i32, [_vp, _P(pc_timing)]),
+    ("pc_submit", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_u64)]),
+    ("pc_poll", _i32, [_vp, _u64, _i32, _P(pc_result)]),
+    ("pc_release_ticket", _i32, [_vp, _u64]),
+]
+
+
+def build(force: bool = False) -> str:
+    """Compile libpcr.so for sm_103a (see build.py)."""
+    return _build_mod.build(force=force)
+
+
+def lib_path() -> str:
+    return _build_mod.SO
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpcr.so (raises if it has not been built for this machine)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build_mod.SO
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: run paper_2204_01287_gb300.build() "
+                                   "(the rasterizer has no CPU fallback)")
+            L = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class PCError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{lib().pc_strerror(status).decode()} ({status}) {msg}".strip())
+
+
+def _check(ctx, rc):
+    if rc != PC_OK:
+        msg = lib().pc_last_error(ctx).decode() if ctx else ""
+        raise PCError(rc, msg)
+
+
+# ---- thin wrappers keeping the C names ---------------------------------------
+
+def pc_config_default() -> pc_config:
+    c = pc_config()
+    lib().pc_config_default(ctypes.byref(c))
+    return c
+
+
+def pc_create(device: int = 0, cfg: pc_config | None = None) -> int:
+    h = ctypes.c_void_p()
+    rc = lib().pc_create(ctypes.byref(h), device, ctypes.byref(cfg) if cfg else None)
+    _check(None, rc)
+    return h.value
+
+
+def pc_destroy(ctx: int) -> None:
+    lib().pc_destroy(ctx)
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def pc_encode(xyz: np.ndarray, rgba: np.ndarray | None, batch_size: int = 10240,
+              threads: int = 0):
+    """Host encoder: returns (batches, w1, w2, w3, color, perm) numpy arrays."""
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    n = xyz.shape[0]
+    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    nb = (n + batch_size - 1) // batch_size
+    batches = np.zeros(nb, BATCH_DTYPE)
+    w = [np.zeros(n, np.uint32) for _ in range(4)]
+    perm = np.zeros(n, np.uint32)
+    rc = lib().pc_encode(_np_ptr(xyz), _np_ptr(rgba), n, batch_size, threads,
+                         _np_ptr(batches), *(x.ctypes.data for x in w), _np_ptr(perm))
+    _check(None, rc)
+    return batches, w[0], w[1], w[2], w[3], perm
+
+
+def pc_upload_cloud(ctx: int, xyz: np.ndarray, rgba: np.ndarray | None) -> int:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    out = ctypes.c_uint64()
+    _check(ctx, lib().pc_upload_cloud(ctx, _np_ptr(xyz), _np_ptr(rgba), xyz.shape[0],
+                                      ctypes.byref(out)))
+    return out.value
+
+
+def pc_upload_encoded(ctx: int, batches, w1, w2, w3, color) -> int:
+    arrs = [np.ascontiguousarray(a, np.uint32) for a in (w1, w2, w3, color)]
+    b = np.ascontiguousarray(batches, BATCH_DTYPE)
+    out = ctypes.c_uint64()
+    _check(ctx, lib().pc_upload_encoded(ctx, _np_ptr(b), len(b), *(a.ctypes.data for a in arrs),
+                                        len(arrs[0]), ctypes.byref(out)))
+    return out.value
+
+
+def pc_cloud_get_info(ctx: int, cloud: int) -> pc_cloud_info:
+    info = pc_cloud_info()
+    _check(ctx, lib().pc_cloud_get_info(ctx, cloud, ctypes.byref(info)))
+    return info
+
+
+def pc_cloud_download(ctx: int, cloud: int):
+    info = pc_cloud_get_info(ctx, cloud)
+    batches = np.zeros(info.n_batches, BATCH_DTYPE)
+    w = [np.zeros(info.n_points, np.uint32) for _ in range(4)]
+    _check(ctx, lib().pc_cloud_download(ctx, cloud, _np_ptr(batches), *(x.ctypes.data for x in w)))
+    return batches, w[0], w[1], w[2], w[3]
+
+
+def pc_release_cloud(ctx: int, cloud: int) -> None:
+    _check(ctx, lib().pc_release_cloud(ctx, cloud))
+
+
+def pc_build_lod(ctx: int, cloud: int, max_levels: int = 12, max_node_points: int = 10240,
+                 seed: int = 0) -> int:
+    o = pc_lod_opts(max_levels, max_node_points, seed, 0)
+    out = ctypes.c_uint64()
+    _check(ctx, lib().pc_build_lod(ctx, cloud, ctypes.byref(o), ctypes.byref(out)))
+    return out.value
+
+
+def make_view(m, width: int, height: int, flags: int = 0, lod_px: float = 0.0) -> pc_view:
+    v = pc_view()
+    mm = np.asarray(m, np.float32).reshape(16)
+    for i in range(16):
+        v.view_proj[i] = float(mm[i])
+    v.width, v.height, v.flags, v.lod_px = int(width), int(height), int(flags), float(lod_px)
+    return v
+
+
+def _views_arr(views):
+    arr = (pc_view * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = v
+    return arr
+
+
+def pc_render(ctx: int, cloud: int, views, fbs, stream: int = 0) -> None:
+    """fbs: list of (vis_ptr, rgba_ptr) device pointers (e.g. tensor.data_ptr())."""
+    va = _views_arr(views)
+    fa = (pc_framebuffer * len(views))()
+    for i, (vis, rgba) in enumerate(fbs):
+        fa[i] = pc_framebuffer(vis, rgba)
+    _check(ctx, lib().pc_render(ctx, cloud, va, len(views), fa, stream))
+
+
+def pc_render_host(ctx: int, cloud: int, views, out_images, stream: int = 0) -> None:
+    """out_images: list of writable numpy uint32 arrays (width*height each)."""
+    va = _views_arr(views)
+    ptrs = (ctypes.c_void_p * len(views))(*[o.ctypes.data for o in out_images])
+    _check(ctx, lib().pc_render_host(ctx, cloud, va, len(views), ptrs, stream))
+
+
+def pc_get_view_stats(ctx: int, view: int = 0, stream: int = 0) -> dict:
+    st = pc_view_stats()
+    _check(ctx, lib().pc_get_view_stats(ctx, stream, view, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pc_timing_begin(ctx: int) -> None:
+    _check(ctx, lib().pc_timing_begin(ctx))
+
+
+def pc_timing_end(ctx: int) -> pc_timing:
+    t = pc_timing()
+    _check(ctx, lib().pc_timing_end(ctx, ctypes.byref(t)))
+    return t
+
+
+def pc_submit(ctx: int, cloud: int, views) -> int:
+    va = _views_arr(views)
+    out = ctypes.c_uint64()
+    _check(ctx, lib().pc_submit(ctx, cloud, va, len(views), ctypes.byref(out)))
+    return out.value
+
+
+def pc_poll(ctx: int, ticket: int, timeout_ms: int = -1):
+    """Returns (status, result) — status PC_OK or PC_ETIMEDOUT; result holds
+    numpy copies of the images when PC_OK."""
+    r = pc_result()
+    rc = lib().pc_poll(ctx, ticket, timeout_ms, ctypes.byref(r))
+    if rc == PC_ETIMEDOUT:
+        return rc, None
+    _check(ctx, rc)
+    imgs = []
+    for v in range(r.nviews):
+        n = r.widths[v] * r.heights[v]
+        imgs.append(np.ctypeslib.as_array(r.rgba[v], shape=(n,)).copy())
+    return rc, {"status": r.status, "images": imgs, "t_submit_ms": r.t_submit_ms,
+                "t_start_ms": r.t_start_ms, "t_done_ms": r.t_done_ms}
+
+
+def pc_release_ticket(ctx: int, ticket: int) -> None:
+    _check(ctx, lib().pc_release_ticket(ctx, ticket))
+
+
+# ---- convenience ------------------------------------------------------------------
+
+class Context:
+    """A pc_ctx on one CUDA device with torch-allocated framebuffers."""
+
+    def __init__(self, device: int = 0, **cfg_fields):
+        cfg = pc_config_default()
+        for k, v in cfg_fields.items():
+            setattr(cfg, k, v)
+        self.device = device
+        self.h = pc_create(device, cfg)
+
+    def close(self):
+        if self.h:
+            pc_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, xyz, rgba=None) -> int:
+        return pc_upload_cloud(self.h, xyz, rgba)
+
+    def upload_encoded(self, batches, w1, w2, w3, color) -> int:
+        return pc_upload_encoded(self.h, batches, w1, w2, w3, color)
+
+    def framebuffers(self, views):
+        """torch (vis, rgba) tensors for each view, on this device."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        return [(torch.empty(v.height * v.width, dtype=torch.int64, device=dev),
+                 torch.empty(v.height * v.width, dtype=torch.int32, device=dev)) for v in views]
+
+    def render(self, cloud, views, fbs=None, stream=None):
+        """Render views into torch framebuffers (allocated when fbs is None)
+        on `stream` (a torch.cuda.Stream; default the current stream)."""
+        import torch
+        if fbs is None:
+            fbs = self.framebuffers(views)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        pc_render(self.h, cloud, views, [(a.data_ptr(), b.data_ptr()) for a, b in fbs],
+                  s.cuda_stream)
+        return fbs
+
+    def stats(self, view=0, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return pc_get_view_stats(self.h, view, s.cuda_stream)
+
+
+def vis_to_numpy(t) -> np.ndarray:
+    """int64 torch visibility buffer -> uint64 numpy array."""
+    return t.cpu().numpy().view(np.uint64)
+
+
+def rgba_to_numpy(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)

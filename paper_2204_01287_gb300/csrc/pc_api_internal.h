@@ -1,0 +1,92 @@
+// pc_api_internal.h — host-side state of a context (api.cpp, serve.cpp).
+#pragma once
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "pc_internal.h"
+
+namespace pcr {
+
+// A resident cloud: device buffers owned by the library.
+struct Cloud {
+    pc_batch* batches = nullptr;
+    uint32_t* w1 = nullptr;
+    uint32_t* w2 = nullptr;
+    uint32_t* w3 = nullptr;
+    uint32_t* color = nullptr;
+    uint32_t* parent = nullptr;   // LOD clouds
+    uint32_t* level = nullptr;
+    uint64_t n_points = 0;
+    uint64_t n_batches = 0;
+    uint64_t n_entries = 0;       // draw-list entries a frame can need
+    uint64_t device_bytes = 0;
+    uint32_t is_lod = 0;
+    uint32_t lod_levels = 0;
+    void free_device();
+    CloudView view() const;
+};
+
+// Scratch and library-owned framebuffers of one stream.
+struct Slot {
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    Scratch scratch{};
+    uint64_t lod_capacity = 0;
+    uint64_t* host_vis = nullptr;     // pc_render_host framebuffers
+    uint32_t* host_rgba = nullptr;
+    uint64_t host_pixels = 0;
+    uint32_t last_nviews = 0;
+    uint64_t last_total_batches = 0;
+    ~Slot();
+};
+
+struct FrameEvents {
+    cudaEvent_t ev[5];   // start, after clear, after cull, after raster, after resolve
+};
+
+struct ServeState;   // serve.cpp
+
+struct Ctx {
+    int device = 0;
+    int num_sms = 1;
+    pc_config cfg{};
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;                          // clouds, slots, timing records
+    std::map<pc_cloud, std::shared_ptr<Cloud>> clouds;
+    std::map<cudaStream_t, std::unique_ptr<Slot>> slots;
+    pc_cloud next_handle = 0;
+    std::mutex err_mu;
+    std::string last_error, err_copy;
+    bool timing_on = false;
+    std::deque<FrameEvents> frame_events;
+    std::atomic<uint64_t> launches{0};
+    std::atomic<uint64_t> raster_launches{0};
+    int tuned_blocks_per_sm[33] = {0};     // autotuner results by views per launch
+    ServeState* serve = nullptr;
+
+    void fail_msg(const char* fmt, ...);
+    pc_status cuda_fail(cudaError_t e, const char* what);
+    double now_ms() const;
+    Slot* slot_for(cudaStream_t st);
+    std::shared_ptr<Cloud> find_cloud(pc_cloud h);
+    pc_status ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes);
+    RasterShape shape_for(uint32_t nviews);
+    pc_status render(const Cloud& cl, const pc_view* views, uint32_t nviews,
+                     const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);
+    pc_status check_device_error(Slot& s);
+};
+
+// serve.cpp
+void serve_shutdown(Ctx& ctx);
+
+}  // namespace pcr

@@ -1,0 +1,125 @@
+// pc_internal.h — types shared by the host side (api.cpp, encoder.cpp,
+// serve.cpp) and the CUDA kernels (raster.cu) of libpcr.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pc.h"
+
+namespace pcr {
+
+constexpr uint32_t kMaxViewsPerLaunch = 32;   // views in one raster launch
+constexpr uint32_t kMaxViewsPerRender = 256;  // views in one pc_render call
+constexpr uint32_t kSegmentPoints = 2048;     // points one warp takes per grab
+constexpr uint32_t kMaxDim = 16384;           // width and height limit
+
+// Counter slots in Scratch::counters.
+enum : uint32_t {
+    C_ENTRIES = 0,   // draw-list entries written by the cull pass
+    C_GRAB = 1,      // entries taken by raster warps
+    C_ERROR = 2,     // device error flag (nonzero = error code)
+    C_ERRINFO = 3,   // first offending value
+    C_COUNT = 8
+};
+
+// Per-view statistics slots in Scratch::stats (uint64 each).
+enum : uint32_t {
+    S_BATCHES = 0,   // batches that passed culling
+    S_BK1 = 1,       // ... with k = 1, 2, 3
+    S_PK1 = 4,       // their points with k = 1, 2, 3
+    S_WORDS = 7,     // coordinate words loaded for this view's launch group
+    S_COUNT = 8
+};
+
+// Device error codes raised by kernels.
+enum : uint32_t {
+    E_NONE = 0,
+    E_ENTRY_RANGE = 1,     // draw-list overflow
+    E_BATCH_RANGE = 2,     // batch outside the point buffers
+    E_INDEX_RANGE = 3,     // visibility key with an index outside the cloud
+};
+
+// One view as the kernels see it (passed by value in a ViewTable).
+struct ViewParams {
+    float m[16];          // world -> clip, column-major
+    uint32_t width, height;
+    uint32_t flags;       // PC_VIEW_*
+    float lod_px;
+    uint64_t* vis;        // device, width*height
+    uint32_t* rgba;       // device, width*height, may be null
+};
+
+// Up to kMaxViewsPerLaunch views; lives in the kernel parameter space so that
+// launches need no host->device copy and can be captured in CUDA graphs.
+struct ViewTable {
+    uint32_t n;
+    float threshold_px;   // precision threshold T
+    ViewParams v[kMaxViewsPerLaunch];
+};
+static_assert(sizeof(ViewTable) < 4000, "ViewTable must fit the kernel parameter space");
+
+// A resident cloud as the kernels see it.
+struct CloudView {
+    const pc_batch* batches;
+    const uint32_t* w1;
+    const uint32_t* w2;
+    const uint32_t* w3;
+    const uint32_t* color;
+    uint64_t n_points;
+    uint32_t n_batches;
+    uint32_t is_lod;
+    const uint32_t* parent;     // LOD: parent node of each batch (root: itself)
+    const uint32_t* level;      // LOD: depth of each node
+};
+
+// One unit of raster work: a segment of at most kSegmentPoints points of a
+// batch, with the views that did not cull the batch and their precisions.
+struct DrawEntry {
+    uint64_t kcodes;      // 2 bits per view: k in 1..3
+    uint32_t view_mask;   // bit v: view v renders this batch
+    uint32_t batch;
+    uint32_t seg_first;   // first point of the segment, relative to the batch
+    uint32_t seg_count;
+};
+
+// Per-stream scratch memory (device).
+struct Scratch {
+    DrawEntry* entries;
+    uint64_t capacity;    // entries
+    uint32_t* counters;   // C_COUNT
+    unsigned long long* stats;  // kMaxViewsPerRender * S_COUNT
+    uint8_t* lod_sel;     // LOD: per node and view group, selected flag (n_batches)
+};
+
+// Launch-shape knobs for the raster kernel.
+struct RasterShape {
+    int threads_per_block;
+    int blocks;            // total persistent blocks
+};
+
+// ---- kernel launchers (raster.cu) ----------------------------------------
+
+cudaError_t launch_clear(const ViewTable& vt, uint32_t view_base, Scratch s,
+                         cudaStream_t st);
+cudaError_t launch_cull(const CloudView& c, const ViewTable& vt, uint32_t view_base,
+                        Scratch s, cudaStream_t st);
+cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, Scratch s,
+                          RasterShape shape, cudaStream_t st);
+cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s,
+                           cudaStream_t st);
+// Blocks per SM the raster kernel can keep resident at a block size.
+int raster_occupancy(int threads_per_block);
+
+// ---- host encoder (encoder.cpp) -------------------------------------------
+
+pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
+                      uint32_t batch_size, unsigned threads, pc_batch* batches,
+                      uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color,
+                      uint32_t* perm);
+
+unsigned hw_threads();
+
+}  // namespace pcr
