@@ -210,6 +210,8 @@ typedef struct {
     uint64_t points_k[4];          /* their points */
     uint64_t points_processed;     /* sum of points_k */
     uint64_t words_loaded_bytes;   /* coordinate bytes the raster launch loaded for this view */
+    uint64_t points_accepted;      /* points that landed inside the viewport */
+    uint64_t points_atomic;        /* points that issued atomicMin (Table 2 "rendered points") */
 } pc_view_stats;
 
 pc_status pc_get_view_stats(pc_ctx* ctx, void* stream, uint32_t view, pc_view_stats* out);

@@ -66,13 +66,15 @@ class pc_view_stats(ctypes.Structure):
     _fields_ = [("batches_total", ctypes.c_uint64), ("batches_rendered", ctypes.c_uint64),
                 ("batches_k", ctypes.c_uint64 * 4), ("points_k", ctypes.c_uint64 * 4),
                 ("points_processed", ctypes.c_uint64),
-                ("words_loaded_bytes", ctypes.c_uint64)]
+                ("words_loaded_bytes", ctypes.c_uint64),
+                ("points_accepted", ctypes.c_uint64), ("points_atomic", ctypes.c_uint64)]
 
     def as_dict(self):
         return {"batches_total": self.batches_total, "batches_rendered": self.batches_rendered,
                 "batches_k": list(self.batches_k), "points_k": list(self.points_k),
                 "points_processed": self.points_processed,
-                "words_loaded_bytes": self.words_loaded_bytes}
+                "words_loaded_bytes": self.words_loaded_bytes,
+                "points_accepted": self.points_accepted, "points_atomic": self.points_atomic}
 
 
 class pc_timing(ctypes.Structure):

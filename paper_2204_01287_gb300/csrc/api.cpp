@@ -126,7 +126,8 @@ std::shared_ptr<Cloud> Ctx::find_cloud(pc_cloud h) {
 RasterShape Ctx::shape_for(uint32_t nviews) {
     RasterShape r;
     r.threads_per_block = cfg.threads_per_block ? (int)cfg.threads_per_block : 256;
-    int per_sm = cfg.blocks_per_sm ? (int)cfg.blocks_per_sm : raster_occupancy(r.threads_per_block);
+    int per_sm = cfg.blocks_per_sm ? (int)cfg.blocks_per_sm
+                                   : raster_occupancy(r.threads_per_block, nviews > 1);
     if (!cfg.blocks_per_sm && tuned_blocks_per_sm[std::min<uint32_t>(nviews, 32)] > 0)
         per_sm = tuned_blocks_per_sm[std::min<uint32_t>(nviews, 32)];
     r.blocks = num_sms * per_sm;
@@ -188,7 +189,7 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
         e = launch_cull(cv, vt, base, slot->scratch, st);
         if (e != cudaSuccess) return cuda_fail(e, "cull launch");
         if (fe) cudaEventRecord(fe->ev[2], st);
-        e = launch_raster(cv, vt, slot->scratch, shape_for(vt.n), st);
+        e = launch_raster(cv, vt, base, slot->scratch, shape_for(vt.n), st);
         if (e != cudaSuccess) return cuda_fail(e, "raster launch");
         if (fe) cudaEventRecord(fe->ev[3], st);
         e = launch_resolve(cv, vt, slot->scratch, st);
@@ -538,6 +539,8 @@ pc_status pc_get_view_stats(pc_ctx* h, void* stream, uint32_t view, pc_view_stat
         out->points_processed += out->points_k[k];
     }
     out->words_loaded_bytes = 4ull * st[S_WORDS];
+    out->points_accepted = st[S_ACCEPTED];
+    out->points_atomic = st[S_ATOMICS];
     return ctx->check_device_error(*slot);
 }
 

@@ -31,7 +31,9 @@ enum : uint32_t {
     S_BK1 = 1,       // ... with k = 1, 2, 3
     S_PK1 = 4,       // their points with k = 1, 2, 3
     S_WORDS = 7,     // coordinate words loaded for this view's launch group
-    S_COUNT = 8
+    S_ACCEPTED = 8,  // points that landed inside the viewport
+    S_ATOMICS = 9,   // points that passed the early-depth test and issued atomicMin
+    S_COUNT = 16
 };
 
 // Device error codes raised by kernels.
@@ -106,12 +108,12 @@ cudaError_t launch_clear(const ViewTable& vt, uint32_t view_base, Scratch s,
                          cudaStream_t st);
 cudaError_t launch_cull(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                         Scratch s, cudaStream_t st);
-cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, Scratch s,
-                          RasterShape shape, cudaStream_t st);
+cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view_base,
+                          Scratch s, RasterShape shape, cudaStream_t st);
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s,
                            cudaStream_t st);
 // Blocks per SM the raster kernel can keep resident at a block size.
-int raster_occupancy(int threads_per_block);
+int raster_occupancy(int threads_per_block, bool multiview);
 
 // ---- host encoder (encoder.cpp) -------------------------------------------
 

@@ -63,6 +63,13 @@ __device__ __forceinline__ float clip_row(const float* m, int r, float x, float 
                      m[r + 12]);
 }
 
+// The same for a row stored contiguously (r0, r1, r2, r3).
+__device__ __forceinline__ float clip_row4(const float* r, float x, float y, float z) {
+    return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)),
+                               __fmul_rn(r[2], z)),
+                     r[3]);
+}
+
 // Unfloored pixel coordinate from a clip coordinate: ((c / w) * 0.5 + 0.5) * W.
 __device__ __forceinline__ float to_pixel(float c, float w, float W) {
     return __fmul_rn(__fadd_rn(__fmul_rn(__fdiv_rn(c, w), 0.5f), 0.5f), W);
@@ -226,18 +233,69 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
     for (uint32_t i = threadIdx.x; i < vt.n * S_COUNT; i += blockDim.x) {
         unsigned long long x = sh_stats[i];
         if (i % S_COUNT == S_WORDS) x = sh_words;   // the whole launch group's word loads
-        if (x) atomicAdd(&s.stats[(uint64_t)view_base * S_COUNT + i], x);
+        if (x && i % S_COUNT <= S_WORDS) atomicAdd(&s.stats[(uint64_t)view_base * S_COUNT + i], x);
     }
 }
 
-// ---- k_raster -------------------------------------------------------------------
-
-// float(u) for u < 2^23, exactly: the bits of 2^23 + u minus 2^23.
-__device__ __forceinline__ float small_u2f(uint32_t u) {
-    return __fsub_rn(__uint_as_float(0x4B000000u | u), 8388608.0f);
+// Hardware reciprocal approximation; used only for w in [2^-100, 2^100], where
+// flushing subnormals cannot matter.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
-// Coordinates of one point at precision k from its words (Sec. 3.3).
+// ---- k_raster -------------------------------------------------------------------
+//
+// Every lane takes an aligned group of 4 consecutive points (one 16-byte load
+// per coordinate word, Sec. 3.4): it decodes and projects all four, then issues
+// the four early-depth reads back to back, then compares and updates. All
+// arithmetic that decides a key or a pixel uses round-to-nearest intrinsics that
+// are never contracted (__fmul_rn, __fadd_rn), in the oracle's order.
+
+// Per-view constants.
+struct ViewConst {
+    float mx[4], my[4], mw[4];  // clip rows x, y, w: (m[r], m[r+4], m[r+8], m[r+12])
+    float W, H;
+    uint32_t width, height;
+    unsigned long long* vis;
+    bool early;
+};
+
+__device__ __forceinline__ ViewConst make_view_const(const ViewParams& v) {
+    ViewConst c;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c.mx[j] = v.m[4 * j + 0];
+        c.my[j] = v.m[4 * j + 1];
+        c.mw[j] = v.m[4 * j + 3];
+    }
+    c.W = (float)v.width;
+    c.H = (float)v.height;
+    c.width = v.width;
+    c.height = v.height;
+    c.vis = reinterpret_cast<unsigned long long*>(v.vis);
+    c.early = !(v.flags & PC_VIEW_NO_EARLY_DEPTH);
+    return c;
+}
+
+// Per-batch decode constants at precision k.
+struct DecConst {
+    float mn[3], cell[3];
+};
+
+__device__ __forceinline__ DecConst make_dec_const(const pc_batch& b, int k) {
+    DecConst d;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d.mn[a] = b.min[a];
+        d.cell[a] = ldexpf(b.size[a], -10 * k);   // exact power-of-two scaling
+    }
+    return d;
+}
+
+// Integer coordinates of one point at precision k from its words (Sec. 3.3):
+// the first k words concatenated from the most significant part down.
 template <int K>
 __device__ __forceinline__ void decode_q(uint32_t a, uint32_t b, uint32_t c, uint32_t& qx,
                                          uint32_t& qy, uint32_t& qz) {
@@ -256,178 +314,240 @@ __device__ __forceinline__ void decode_q(uint32_t a, uint32_t b, uint32_t c, uin
     }
 }
 
+// float(q): exact for q < 2^23 through the bits of 2^23 + q minus 2^23;
+// rounded to nearest for the 30-bit values of k = 3, as (float)q.
 template <int K>
-__device__ __forceinline__ float q2f(uint32_t q) {
-    if (K <= 2) return small_u2f(q);   // q < 2^20: exact
-    return __uint2float_rn(q);         // q < 2^30: rounded to nearest, as (float)q
+__device__ __forceinline__ float q_to_float(uint32_t q) {
+    if (K <= 2) return __fsub_rn(__uint_as_float(0x4B000000u | q), 8388608.0f);
+    return __uint2float_rn(q);
 }
 
-struct Decoder {
-    float mn[3], cell[3];
-};
+// Decoded position (Sec. 3.3): x = min + float(X) * cell per axis, binary32.
+template <int K>
+__device__ __forceinline__ void decode_point(const DecConst& d, uint32_t a, uint32_t b, uint32_t c,
+                                             float& x, float& y, float& z) {
+    uint32_t qx, qy, qz;
+    decode_q<K>(a, b, c, qx, qy, qz);
+    x = __fadd_rn(d.mn[0], __fmul_rn(q_to_float<K>(qx), d.cell[0]));
+    y = __fadd_rn(d.mn[1], __fmul_rn(q_to_float<K>(qy), d.cell[1]));
+    z = __fadd_rn(d.mn[2], __fmul_rn(q_to_float<K>(qz), d.cell[2]));
+}
 
-__device__ __forceinline__ Decoder make_decoder(const pc_batch& b, int k) {
-    Decoder d;
+// Floor bits of the pixel coordinate of one axis: the bits of 2^23 + f rounded
+// down, f = ((c / w) * 0.5 + 0.5) * W. For 0 <= f < 2^23 they are
+// 2^23 + floor(f); every other f (negative, >= 2^23, inf, NaN) lands outside
+// [2^23, 2^24) and fails the range test. The map from f is monotonic.
+//
+// Exact path, the definition through the IEEE divide. (c/w) * 0.5 is exact,
+// or below 2^-126 where the sum rounds to 0.5 either way, so the fused
+// multiply-add equals the separate multiply and add.
+__device__ __forceinline__ uint32_t exact_floor_bits(float c, float w, float W) {
+    const float f = __fmul_rn(__fmaf_rn(__fdiv_rn(c, w), 0.5f, 0.5f), W);
+    return __float_as_uint(__fadd_rd(f, 8388608.0f));
+}
+
+// Certified fast path. q' = c * r with r the reciprocal of w refined by one
+// Newton step (relative error below 2^-40 + 2^-24) is within |q'| 2^-22 of the
+// IEEE quotient. With eta = 2^-21, u- = fl(q' * 0.5 + (0.5 - eta)) and
+// u+ = fl(q' * 0.5 + (0.5 + eta)) bracket the definition's fl(q * 0.5 + 0.5)
+// with room for the roundings of both sides whenever |q'| <= 1.01, so
+// fl_down(u- * W + 2^23) <= floor bits <= fl_down(u+ * W + 2^23); when the two
+// ends agree they are the floor bits. Points with |q'| > 1.01 lie outside the
+// viewport either way. Returns false (use the exact path) when they differ.
+__device__ __forceinline__ bool fast_floor_bits(float c, float r, float W, uint32_t& bits) {
+    const float q = __fmul_rn(c, r);
+    const float ulo = __fmaf_rn(q, 0.5f, 0.5f - 0x1.0p-21f);
+    const float uhi = __fmaf_rn(q, 0.5f, 0.5f + 0x1.0p-21f);
+    const uint32_t blo = __float_as_uint(__fmaf_rd(ulo, W, 8388608.0f));
+    const uint32_t bhi = __float_as_uint(__fmaf_rd(uhi, W, 8388608.0f));
+    bits = blo;
+    return blo == bhi;
+}
+
+// Floor bits of both axes of one point with w > 0.
+__device__ __forceinline__ void pixel_bits(float cx, float cy, float cw, float W, float H,
+                                           uint32_t& bx, uint32_t& by) {
+    float r = rcp_approx(cw);
+    r = __fmaf_rn(r, __fmaf_rn(-cw, r, 1.0f), r);
+    const bool ok = fast_floor_bits(cx, r, W, bx) & fast_floor_bits(cy, r, H, by) &
+                    (cw >= 0x1.0p-100f) & (cw <= 0x1.0p100f);
+    if (!ok) {
+        bx = exact_floor_bits(cx, cw, W);
+        by = exact_floor_bits(cy, cw, H);
+    }
+}
+
+// Listing 1 for the four points of a group: project, test, then the
+// early-depth reads of all four, then atomicMin of (bits(w) << 32 | index)
+// where the key is smaller. A stale early-depth read is larger than or equal
+// to the current value, so it can only cause an unnecessary atomic, never a
+// missed one. A key sent to a pixel is carried to the next point of the group
+// when it lands on the same pixel, so consecutive points (Morton order makes
+// them neighbours) do not repeat the atomic. PARTIAL groups carry a validity
+// mask. Returns the number of atomicMin issued.
+template <bool PARTIAL>
+__device__ __forceinline__ uint32_t raster_quad(const ViewConst& vc, const float (&x)[4],
+                                                const float (&y)[4], const float (&z)[4],
+                                                uint32_t idx0, uint32_t valid) {
+    unsigned long long key[4];
+    uint32_t pix[4];
+    bool live[4];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        d.mn[a] = b.min[a];
-        d.cell[a] = ldexpf(b.size[a], -10 * k);   // exact power-of-two scaling
+    for (int j = 0; j < 4; ++j) {
+        const float cx = clip_row4(vc.mx, x[j], y[j], z[j]);
+        const float cy = clip_row4(vc.my, x[j], y[j], z[j]);
+        const float cw = clip_row4(vc.mw, x[j], y[j], z[j]);
+        live[j] = cw > 0.0f;
+        if (PARTIAL) live[j] = live[j] && ((valid >> j) & 1u);
+        uint32_t bx = 0, by = 0;
+        if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
+        const uint32_t px = bx - 0x4B000000u, py = by - 0x4B000000u;
+        live[j] = live[j] && px < vc.width && py < vc.height;
+        key[j] = ((unsigned long long)__float_as_uint(cw) << 32) | (unsigned long long)(idx0 + j);
+        pix[j] = py * vc.width + px;
     }
-    return d;
+    unsigned long long old[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) old[j] = (live[j] && vc.early) ? vc.vis[pix[j]] : ~0ull;
+    uint32_t n_atom = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (live[j] && key[j] < old[j]) {
+            atomicMin(vc.vis + pix[j], key[j]);
+            ++n_atom;
+            if (j < 3 && pix[j + 1] == pix[j] && key[j] < old[j + 1]) old[j + 1] = key[j];
+        }
+    }
+    return n_atom;
 }
 
-// Listing 1 for one decoded point and one view: project, test, early depth,
-// atomicMin of (bits(w) << 32 | idx).
-__device__ __forceinline__ void raster_point(float x, float y, float z, uint32_t idx,
-                                             const ViewParams& v, bool early) {
-    const float* m = v.m;
-    const float cx = clip_row(m, 0, x, y, z);
-    const float cy = clip_row(m, 1, x, y, z);
-    const float cw = clip_row(m, 3, x, y, z);
-    if (!(cw > 0.0f)) return;
-    // ((c / w) * 0.5 + 0.5) * W: c/w * 0.5 is exact (or below 2^-126, where the
-    // sum rounds to 0.5 either way), so one fused multiply-add gives the same
-    // value as the separate multiply and add.
-    const float fx = __fmul_rn(__fmaf_rn(__fdiv_rn(cx, cw), 0.5f, 0.5f), (float)v.width);
-    const float fy = __fmul_rn(__fmaf_rn(__fdiv_rn(cy, cw), 0.5f, 0.5f), (float)v.height);
-    // floor and range test in one: for 0 <= f < 2^23, 2^23 + f rounded down is
-    // 2^23 + floor(f); every other f (negative, >= 2^23, inf, NaN) maps to an
-    // integer outside [0, 2^23) after subtracting the bits of 2^23.
-    const int px = __float_as_int(__fadd_rd(fx, 8388608.0f)) - 0x4B000000;
-    const int py = __float_as_int(__fadd_rd(fy, 8388608.0f)) - 0x4B000000;
-    if ((uint32_t)px >= v.width || (uint32_t)py >= v.height) return;
-    const unsigned long long key =
-        ((unsigned long long)__float_as_uint(cw) << 32) | (unsigned long long)idx;
-    unsigned long long* addr =
-        reinterpret_cast<unsigned long long*>(v.vis) + ((size_t)py * v.width + (uint32_t)px);
-    if (early) {
-        // a stale read is larger than or equal to the current value, so it
-        // can only cause an unnecessary atomic, never a missed one
-        if (key < *addr) atomicMin(addr, key);
-    } else {
-        atomicMin(addr, key);
-    }
-}
-
-__device__ __forceinline__ uint4 ld_stream(const uint32_t* p) {
+template <bool STREAM>
+__device__ __forceinline__ uint4 ld_words(const uint32_t* p) {
     uint4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
+    if (STREAM)
+        asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                     : "l"(p));
+    else
+        asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                     : "l"(p));
     return r;
 }
 
-__device__ __forceinline__ uint32_t pick(const uint4& q, int j) {
-    return j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
-}
-
-// Process the aligned groups of 4 points of [p0, p1) for the views of mask at
-// precision KL words loaded; each view decodes with its own k <= KL.
-template <int KL>
-__device__ __forceinline__ void raster_segment(const CloudView& c, const ViewTable& vt,
-                                               const pc_batch& bt, uint64_t p0, uint64_t p1,
-                                               uint32_t mask, uint64_t kcodes, uint32_t lane) {
-    const uint64_t a0 = p0 & ~3ull;
-    for (uint64_t g = a0 + 4ull * lane; g < p1; g += 128ull) {
-        uint4 q1 = ld_stream(c.w1 + g);
+// Points [p0, p1) of one batch for one view at precision K. The loop over
+// groups of 4 is warp-uniform; STREAM loads bypass L1 (single view), the
+// multi-view kernel keeps the words in cache for the next view.
+template <int K, bool STREAM>
+__device__ __forceinline__ uint32_t segment(const CloudView& c, const ViewConst& vc,
+                                            const DecConst& d, uint32_t p0, uint32_t p1,
+                                            uint32_t lane) {
+    uint32_t n_atom = 0;
+    for (uint32_t base = p0 & ~3u; base < p1; base += 128u) {
+        const uint32_t g = base + 4u * lane;
+        if (g >= p1) continue;
+        const uint4 q1 = ld_words<STREAM>(c.w1 + g);
         uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
-        if (KL >= 2) q2 = ld_stream(c.w2 + g);
-        if (KL >= 3) q3 = ld_stream(c.w3 + g);
-        uint32_t mm = mask;
-        while (mm) {
-            const uint32_t v = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const ViewParams& vp = vt.v[v];
-            const int k = (int)((kcodes >> (2 * v)) & 3u);
-            const Decoder d = make_decoder(bt, k);
-            const bool early = !(vp.flags & PC_VIEW_NO_EARLY_DEPTH);
+        if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
+        if (K >= 3) q3 = ld_words<STREAM>(c.w3 + g);
+        float x[4], y[4], z[4];
+        decode_point<K>(d, q1.x, q2.x, q3.x, x[0], y[0], z[0]);
+        decode_point<K>(d, q1.y, q2.y, q3.y, x[1], y[1], z[1]);
+        decode_point<K>(d, q1.z, q2.z, q3.z, x[2], y[2], z[2]);
+        decode_point<K>(d, q1.w, q2.w, q3.w, x[3], y[3], z[3]);
+        if (g >= p0 && g + 4u <= p1) {
+            n_atom += raster_quad<false>(vc, x, y, z, g, 0xFu);
+        } else {
+            uint32_t valid = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint64_t i = g + j;
-                if (i < p0 || i >= p1) continue;
-                uint32_t qx, qy, qz;
-                float fx, fy, fz;
-                const uint32_t a = pick(q1, j), b = pick(q2, j), cc = pick(q3, j);
-                if (k == 1) {
-                    decode_q<1>(a, b, cc, qx, qy, qz);
-                    fx = q2f<1>(qx); fy = q2f<1>(qy); fz = q2f<1>(qz);
-                } else if (k == 2) {
-                    decode_q<2>(a, b, cc, qx, qy, qz);
-                    fx = q2f<2>(qx); fy = q2f<2>(qy); fz = q2f<2>(qz);
-                } else {
-                    decode_q<3>(a, b, cc, qx, qy, qz);
-                    fx = q2f<3>(qx); fy = q2f<3>(qy); fz = q2f<3>(qz);
-                }
-                const float x = __fadd_rn(d.mn[0], __fmul_rn(fx, d.cell[0]));
-                const float y = __fadd_rn(d.mn[1], __fmul_rn(fy, d.cell[1]));
-                const float z = __fadd_rn(d.mn[2], __fmul_rn(fz, d.cell[2]));
-                raster_point(x, y, z, (uint32_t)i, vp, early);
-            }
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
+            n_atom += raster_quad<true>(vc, x, y, z, g, valid);
         }
     }
-}
-
-// Single view at precision K: the common case, with everything warp-uniform.
-template <int K>
-__device__ __forceinline__ void raster_segment_1view(const CloudView& c, const ViewParams& vp,
-                                                     const pc_batch& bt, uint64_t p0,
-                                                     uint64_t p1, uint32_t lane) {
-    const Decoder d = make_decoder(bt, K);
-    const bool early = !(vp.flags & PC_VIEW_NO_EARLY_DEPTH);
-    const uint64_t a0 = p0 & ~3ull;
-    for (uint64_t g = a0 + 4ull * lane; g < p1; g += 128ull) {
-        uint4 q1 = ld_stream(c.w1 + g);
-        uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
-        if (K >= 2) q2 = ld_stream(c.w2 + g);
-        if (K >= 3) q3 = ld_stream(c.w3 + g);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint64_t i = g + j;
-            if (i < p0 || i >= p1) continue;
-            uint32_t qx, qy, qz;
-            decode_q<K>(pick(q1, j), pick(q2, j), pick(q3, j), qx, qy, qz);
-            const float x = __fadd_rn(d.mn[0], __fmul_rn(q2f<K>(qx), d.cell[0]));
-            const float y = __fadd_rn(d.mn[1], __fmul_rn(q2f<K>(qy), d.cell[1]));
-            const float z = __fadd_rn(d.mn[2], __fmul_rn(q2f<K>(qz), d.cell[2]));
-            raster_point(x, y, z, (uint32_t)i, vp, early);
-        }
-    }
+    return n_atom;
 }
 
 constexpr int kRasterThreads = 256;
 
-__global__ void __launch_bounds__(kRasterThreads) k_raster(CloudView c, ViewTable vt, Scratch s) {
+__device__ __forceinline__ bool next_entry(const Scratch& s, uint32_t n_entries, uint32_t lane,
+                                           DrawEntry& e) {
+    uint32_t e_idx = 0;
+    if (lane == 0) e_idx = atomicAdd(&s.counters[C_GRAB], 1u);
+    e_idx = __shfl_sync(FULL, e_idx, 0);
+    if (e_idx >= n_entries || e_idx >= s.capacity) return false;
+    e = s.entries[e_idx];
+    return true;
+}
+
+template <bool STREAM>
+__device__ __forceinline__ uint32_t segment_k(const CloudView& c, const ViewConst& vc,
+                                              const pc_batch& bt, int k, uint32_t p0, uint32_t p1,
+                                              uint32_t lane) {
+    const DecConst d = make_dec_const(bt, k);
+    if (k == 1) return segment<1, STREAM>(c, vc, d, p0, p1, lane);
+    if (k == 2) return segment<2, STREAM>(c, vc, d, p0, p1, lane);
+    return segment<3, STREAM>(c, vc, d, p0, p1, lane);
+}
+
+__device__ __forceinline__ void flush_atomics(const Scratch& s, uint32_t view, uint32_t n_atom,
+                                              uint32_t lane) {
+    const uint32_t t = __reduce_add_sync(FULL, n_atom);
+    if (lane == 0 && t)
+        atomicAdd(&s.stats[(uint64_t)view * S_COUNT + S_ATOMICS], (unsigned long long)t);
+}
+
+// One view per launch: persistent warps take draw-list segments.
+__global__ void __launch_bounds__(kRasterThreads) k_raster1(CloudView c, ViewTable vt,
+                                                           uint32_t view_base, Scratch s) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n_entries = s.counters[C_ENTRIES];
-    for (;;) {
-        uint32_t e_idx = 0;
-        if (lane == 0) e_idx = atomicAdd(&s.counters[C_GRAB], 1u);
-        e_idx = __shfl_sync(FULL, e_idx, 0);
-        if (e_idx >= n_entries || e_idx >= s.capacity) break;
-        const DrawEntry e = s.entries[e_idx];
+    const ViewConst vc = make_view_const(vt.v[0]);
+    uint32_t n_atom = 0;
+    DrawEntry e;
+    while (next_entry(s, n_entries, lane, e)) {
         if (e.batch >= c.n_batches) {
             if (lane == 0) raise_error(s, E_BATCH_RANGE, e.batch);
             continue;
         }
         const pc_batch bt = c.batches[e.batch];
-        const uint64_t p0 = (uint64_t)bt.first + e.seg_first;
-        const uint64_t p1 = p0 + e.seg_count;
-        uint32_t kl = 0;
+        const uint32_t p0 = bt.first + e.seg_first;
+        n_atom += segment_k<true>(c, vc, bt, (int)(e.kcodes & 3u), p0, p0 + e.seg_count, lane);
+    }
+    flush_atomics(s, view_base, n_atom, lane);
+}
+
+// Several views per launch (Sec. 3.7): a warp walks each segment once per view
+// that did not cull its batch; the first walk brings the words from HBM, the
+// others find them in cache. Every view decodes at its own precision.
+__global__ void __launch_bounds__(kRasterThreads) k_rasterN(CloudView c, ViewTable vt,
+                                                           uint32_t view_base, Scratch s) {
+    __shared__ uint32_t sh_atom[kMaxViewsPerLaunch];
+    for (uint32_t i = threadIdx.x; i < kMaxViewsPerLaunch; i += blockDim.x) sh_atom[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n_entries = s.counters[C_ENTRIES];
+    DrawEntry e;
+    while (next_entry(s, n_entries, lane, e)) {
+        if (e.batch >= c.n_batches) {
+            if (lane == 0) raise_error(s, E_BATCH_RANGE, e.batch);
+            continue;
+        }
+        const pc_batch bt = c.batches[e.batch];
+        const uint32_t p0 = bt.first + e.seg_first;
         for (uint32_t mm = e.view_mask; mm; mm &= mm - 1) {
             const uint32_t v = __ffs(mm) - 1;
-            kl = max(kl, (uint32_t)((e.kcodes >> (2 * v)) & 3u));
-        }
-        if (e.view_mask == 1u) {
-            const ViewParams& vp = vt.v[0];
-            if (kl == 1) raster_segment_1view<1>(c, vp, bt, p0, p1, lane);
-            else if (kl == 2) raster_segment_1view<2>(c, vp, bt, p0, p1, lane);
-            else raster_segment_1view<3>(c, vp, bt, p0, p1, lane);
-        } else {
-            if (kl == 1) raster_segment<1>(c, vt, bt, p0, p1, e.view_mask, e.kcodes, lane);
-            else if (kl == 2) raster_segment<2>(c, vt, bt, p0, p1, e.view_mask, e.kcodes, lane);
-            else raster_segment<3>(c, vt, bt, p0, p1, e.view_mask, e.kcodes, lane);
+            const ViewConst vc = make_view_const(vt.v[v]);
+            const uint32_t n = segment_k<false>(c, vc, bt, (int)((e.kcodes >> (2 * v)) & 3u),
+                                                p0, p0 + e.seg_count, lane);
+            const uint32_t t = __reduce_add_sync(FULL, n);
+            if (lane == 0 && t) atomicAdd(&sh_atom[v], t);
         }
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < vt.n; i += blockDim.x)
+        if (sh_atom[i])
+            atomicAdd(&s.stats[(uint64_t)(view_base + i) * S_COUNT + S_ATOMICS],
+                      (unsigned long long)sh_atom[i]);
 }
 
 // ---- k_resolve ---------------------------------------------------------------------
@@ -485,20 +605,23 @@ cudaError_t launch_cull(const CloudView& c, const ViewTable& vt, uint32_t view_b
     return cudaGetLastError();
 }
 
-int raster_occupancy(int threads_per_block) {
+int raster_occupancy(int threads_per_block, bool multiview) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_raster, threads_per_block, 0) !=
-        cudaSuccess)
-        return 1;
+    cudaError_t e = multiview
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rasterN, threads_per_block, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_raster1, threads_per_block, 0);
+    if (e != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, Scratch s, RasterShape shape,
-                          cudaStream_t st) {
+cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view_base, Scratch s,
+                          RasterShape shape, cudaStream_t st) {
     int threads = shape.threads_per_block > 0 ? shape.threads_per_block : kRasterThreads;
-    if (threads > kRasterThreads) threads = kRasterThreads;
-    int blocks = shape.blocks > 0 ? shape.blocks : num_sms() * raster_occupancy(threads);
-    k_raster<<<blocks, threads, 0, st>>>(c, vt, s);
+    threads = threads > kRasterThreads ? kRasterThreads : (threads < 32 ? 32 : threads & ~31);
+    const bool multi = vt.n > 1;
+    int blocks = shape.blocks > 0 ? shape.blocks : num_sms() * raster_occupancy(threads, multi);
+    if (multi) k_rasterN<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
+    else k_raster1<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ def test_unit_cube_forced_k3(ctx, n, W, H):
     [(vis, img)] = gpu_render(ctx, cloud, [pcr.make_view(m, W, H, pcr.PC_VIEW_FORCE_K(3))])
     ovis, st = O.render(enc, oracle_view(m, W, H, force_k=3))
     assert_same(vis, img, ovis, enc.color, "cube")
-    assert (ovis != O.EMPTY).sum() > 0.5 * W * H
+    assert (ovis != O.EMPTY).sum() > 0.1 * W * H
     gst = ctx.stats()
     assert gst["points_k"][3] == n and gst["batches_rendered"] == len(enc.batches)
 
@@ -252,3 +252,64 @@ def test_invalid_arguments(ctx):
     bad[0]["first"], bad[0]["count"] = 10, 100
     with pytest.raises(pcr.PCError):
         pcr.pc_upload_encoded(ctx.h, bad, *[np.zeros(50, np.uint32)] * 4)
+
+
+def _manual_cloud(pos, bmin, bsize, color=None):
+    """One batch encoded against a caller-given box (oracle Eq. 1 + Listing 2)."""
+    n = len(pos)
+    b = np.zeros(1, O.BATCH_DTYPE)
+    b[0]["min"], b[0]["size"], b[0]["first"], b[0]["count"] = bmin, bsize, 0, n
+    w = np.array([O.split_words(*(O.quantize30(p[a], bmin[a], bsize[a]) for a in range(3)))
+                  for p in pos], np.uint32).reshape(n, 3)
+    col = np.arange(n, dtype=np.uint32) + 1 if color is None else color
+    return O.Encoded(b, w[:, 0].copy(), w[:, 1].copy(), w[:, 2].copy(), col,
+                     np.arange(n, dtype=np.uint32))
+
+
+def test_points_on_pixel_edges(ctx):
+    """Orthographic camera (w = 1) and positions whose pixel coordinate is an
+    exact integer or one ulp away from it: the certified fast pixel path must
+    hand these to the IEEE-divide path and agree with the oracle."""
+    W, H = 64, 32
+    rng = np.random.default_rng(12)
+    m = np.zeros(16, np.float32)
+    m[0] = m[5] = m[10] = m[15] = 1.0
+    i = rng.integers(0, W + 1, 3000)
+    jx = (2.0 * i / W - 1.0).astype(np.float32)
+    jy = (2.0 * rng.integers(0, H + 1, 3000) / H - 1.0).astype(np.float32)
+    nudge = rng.integers(-1, 2, 3000)
+    jx = np.nextafter(jx, np.where(nudge > 0, 2, -2).astype(np.float32)) * (nudge != 0) + jx * (nudge == 0)
+    pos = np.stack([jx.astype(np.float32), jy, rng.uniform(-0.9, 0.9, 3000).astype(np.float32)], 1)
+    enc = _manual_cloud(pos, (-1.0, -1.0, -1.0), (2.0, 2.0, 2.0))
+    cloud = ctx.upload_encoded(enc.batches, enc.w1, enc.w2, enc.w3, enc.color)
+    for k in (1, 2, 3):
+        [(vis, img)] = gpu_render(ctx, cloud, [pcr.make_view(m, W, H, pcr.PC_VIEW_FORCE_K(k))])
+        ovis, _ = O.render(enc, oracle_view(m, W, H, force_k=k))
+        assert_same(vis, img, ovis, enc.color, f"edges k={k}")
+
+
+@pytest.mark.parametrize("scale_exp", [-110, -60, 0, 60, 110])
+def test_matrix_power_of_two_scale(ctx, terrain_small, scale_exp):
+    """Scaling the whole matrix by 2^s scales every clip coordinate exactly, so
+    pixels and images stay the same; |w| outside [2^-100, 2^100] forces the
+    IEEE-divide path for every point."""
+    p, enc, cloud = terrain_small
+    W, H = 200, 110
+    m = S.random_view(p, 21, W, H, seed=2).astype(np.float64)
+    ms = (m * 2.0**scale_exp).astype(np.float32)
+    [(vis, img)] = gpu_render(ctx, cloud, [pcr.make_view(ms, W, H, pcr.PC_VIEW_CULL)])
+    ovis, _ = O.render(enc, oracle_view(ms, W, H))
+    assert_same(vis, img, ovis, enc.color, f"scale 2^{scale_exp}")
+    [(vis0, img0)] = gpu_render(ctx, cloud, [pcr.make_view(m.astype(np.float32), W, H,
+                                                           pcr.PC_VIEW_CULL)])
+    assert np.array_equal(img, img0)
+
+
+def test_large_view(ctx, terrain_small):
+    """16384 x 64 view: the certification margin scales with the width."""
+    p, enc, cloud = terrain_small
+    W, H = 16384, 64
+    m = S.random_view(p, 31, W, H, seed=2)
+    [(vis, img)] = gpu_render(ctx, cloud, [pcr.make_view(m, W, H, pcr.PC_VIEW_CULL)])
+    ovis, _ = O.render(enc, oracle_view(m, W, H))
+    assert_same(vis, img, ovis, enc.color, "wide view")
