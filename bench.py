@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=8e6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--serve-rate", type=float, default=4000.0,
+                    help="Poisson arrival rate of requests per second (offered load)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
 
@@ -163,6 +168,99 @@ def cpu_baseline(args, params, m, sample_points, threads=None):
     return pps, cores, desc, enc, v
 
 
+def serving_bench(args, pcr, ctx, clouds):
+    """Poisson stream of view requests over resident clouds, served with
+    multi-view batching and with one view per launch; same requests, same
+    bits. Returns the serving summary."""
+    import hashlib
+    import pcsynth
+    rng = np.random.default_rng(args.seed + 101)
+    choices = [(1280, 720), (1920, 1080), (3840, 2160), "stereo"]
+    reqs, t = [], 0.0
+    for i in range(args.serve_requests):
+        t += rng.exponential(1.0 / args.serve_rate)
+        cloud, params, name = clouds[int(rng.integers(len(clouds)))]
+        c = choices[int(rng.integers(len(choices)))]
+        if c == "stereo":
+            W, H = 2016, 2240
+            views = [pcr.make_view(pcsynth.stereo(params, W, H, e, 6.5), W, H, pcr.PC_VIEW_CULL)
+                     for e in (0, 1)]
+        else:
+            W, H = c
+            views = [pcr.make_view(pcsynth.random_view(params, i, W, H, seed=args.seed), W, H,
+                                   pcr.PC_VIEW_CULL)]
+        reqs.append((t, cloud, views))
+
+    def run(vpl):
+        pcr.pc_set_views_per_launch(ctx.h, vpl)
+        tickets, results = [], [None] * len(reqs)
+        lock = threading.Condition()
+        done_submitting = [False]
+
+        def collect():
+            k = 0
+            while True:
+                with lock:
+                    while k >= len(tickets) and not done_submitting[0]:
+                        lock.wait(0.05)
+                    if k >= len(tickets):
+                        return
+                    tk = tickets[k]
+                rc, res = pcr.pc_poll(ctx.h, tk, 60000)
+                if rc != pcr.PC_OK:
+                    raise RuntimeError("serving request did not finish within 60 s")
+                h = hashlib.sha256()
+                for img in res["images"]:
+                    h.update(img.tobytes())
+                results[k] = (res["t_submit_ms"], res["t_done_ms"], h.hexdigest(), res["status"])
+                pcr.pc_release_ticket(ctx.h, tk)
+                k += 1
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        for ta, cloud, views in reqs:
+            d = ta - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            while True:
+                try:
+                    tk = pcr.pc_submit(ctx.h, cloud, views)
+                    break
+                except pcr.PCError as e:
+                    if e.status != pcr.PC_EBUSY:
+                        raise
+                    time.sleep(0.0005)   # pinned image memory full: wait for the collector
+            with lock:
+                tickets.append(tk)
+                lock.notify_all()
+        with lock:
+            done_submitting[0] = True
+            lock.notify_all()
+        th.join()
+        t_sub = min(r[0] for r in results)
+        t_done = max(r[1] for r in results)
+        lat = np.array([r[1] - r[0] for r in results])
+        nviews = sum(len(v) for _, _, v in reqs)
+        return {"views_per_s": nviews / ((t_done - t_sub) / 1e3),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "ok": all(r[3] == pcr.PC_OK for r in results)}, [r[2] for r in results]
+
+    run(32)   # warm-up: streams, pools, graphs
+    batched, hb = run(32)
+    single, hs = run(1)
+    pcr.pc_set_views_per_launch(ctx.h, 32)
+    return {"requests": len(reqs), "views": sum(len(v) for _, _, v in reqs),
+            "offered_rate_req_per_s": args.serve_rate,
+            "clouds": [c[2] for c in clouds],
+            "resolutions": "1280x720 / 1920x1080 / 3840x2160 / stereo 2x2016x2240, uniform",
+            "views_per_s": batched["views_per_s"], "p50_ms": batched["p50_ms"],
+            "p99_ms": batched["p99_ms"],
+            "one_view_per_launch": single,
+            "speedup_vs_one_view_per_launch": batched["views_per_s"] / single["views_per_s"],
+            "identical_bits": hb == hs, "all_ok": batched["ok"] and single["ok"]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -219,7 +317,7 @@ def main():
     pcsynth.terrain(n, params, seed=args.seed, out=(xyz, rgba))
     t_gen = time.perf_counter() - t0
     log(args, f"generated {n:,} points in {t_gen:.1f}s")
-    ctx = pcr.Context(local)
+    ctx = pcr.Context(local, serve_pool_bytes=12 << 30, serve_streams=4, flags=pcr.PC_CFG_GRAPHS)
     t0 = time.perf_counter()
     cloud = ctx.upload(xyz, rgba)
     t_up = time.perf_counter() - t0
@@ -230,6 +328,10 @@ def main():
     view = pcr.make_view(m, W, H, pcr.PC_VIEW_CULL)
     fbs = ctx.framebuffers([view])
     stream = torch.cuda.current_stream()
+    tune = None
+    if not args.no_autotune:
+        tune = pcr.pc_autotune(ctx.h, cloud, [view], stream.cuda_stream)
+        log(args, f"autotune: {tune}")
     for _ in range(max(args.warmup, 3)):
         ctx.render(cloud, [view], fbs)
     torch.cuda.synchronize()
@@ -277,6 +379,20 @@ def main():
               "resolve_ms": timing.ms_resolve / max(1, timing.frames),
               "frame_hbm_frac": frame_bytes / (ms_per_frame / 1e3) / 1e9 / peak}
 
+    # the same frames replayed through a captured CUDA graph (no per-pass events)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            ctx.render(cloud, [view], fbs, stream=side)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(side)
+        for _ in range(args.steps):
+            ctx.render(cloud, [view], fbs, stream=side)
+        g1.record(side)
+    side.synchronize()
+    passes["graph_replay_ms_per_frame"] = g0.elapsed_time(g1) / args.steps
+
     e2e = None
     if not args.no_e2e:
         host = torch.empty(W * H, dtype=torch.int32, pin_memory=True)
@@ -292,6 +408,20 @@ def main():
                "h2d_bytes_per_step": int(np.dtype(np.uint8).itemsize * 80),
                "d2h_bytes_per_step": W * H * 4, "steps": k2,
                "ms_per_step": dt / k2 * 1e3, "api": "pc_render_host"}
+
+    serving = None
+    if not args.no_serving:
+        clouds = [(cloud, params, f"{n:,} points (the cloud above)")]
+        for npts, seed_off in ((int(4e8), 1), (int(1e7), 2)):
+            if npts >= n:
+                continue
+            x2 = np.empty((npts, 3), np.float32)
+            r2 = np.empty(npts, np.uint32)
+            pcsynth.terrain(npts, params, seed=args.seed + seed_off, out=(x2, r2))
+            clouds.append((ctx.upload(x2, r2), params, f"{npts:,} points"))
+            del x2, r2
+        serving = serving_bench(args, pcr, ctx, clouds)
+        log(args, f"serving: {serving}")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -314,6 +444,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "setup_s": {"generate": t_gen, "encode_upload": t_up}},
                 "roofline": roofline, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
+                "serving": serving, "autotune": tune,
                 "gpu_launches": int(timing.launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     ctx.close()

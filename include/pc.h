@@ -54,6 +54,8 @@ typedef uint64_t pc_ticket;   /* 0 is never a valid ticket */
 /* ---- configuration ------------------------------------------------------ */
 
 #define PC_CFG_TIMING 1u      /* record per-pass CUDA events in pc_render */
+#define PC_CFG_GRAPHS 2u      /* replay each frame's kernels as a captured CUDA graph
+                                 (updated in place when the views change) */
 
 typedef struct {
     uint32_t batch_size;          /* points per batch, multiple of 4 (default 10240, Sec. 3.1) */
@@ -215,6 +217,34 @@ typedef struct {
 } pc_view_stats;
 
 pc_status pc_get_view_stats(pc_ctx* ctx, void* stream, uint32_t view, pc_view_stats* out);
+
+/* ---- autotuner ------------------------------------------------------------- */
+
+typedef struct {
+    uint32_t threads_per_block;   /* raster block size chosen */
+    uint32_t blocks_per_sm;       /* resident raster blocks per SM chosen */
+    uint32_t points_per_warp;     /* points a raster warp takes per grab (points per
+                                     thread = points_per_warp / 32) */
+    uint32_t views_per_launch;    /* views rendered by one launch (multi-view) */
+    double   ms_per_view;         /* best time per view measured */
+    double   ms_per_view_single;  /* time per view at one view per launch, same shape */
+    uint32_t candidates;          /* configurations timed */
+    uint32_t reserved;
+} pc_tune_result;
+
+/* Time candidate raster launch shapes (threads per block, blocks per SM,
+ * points per warp grab) on views[0], then candidate views per launch on all
+ * nviews views, all on `stream` with library-owned framebuffers, and keep the
+ * fastest for later pc_render and serving launches on this context (fields set
+ * in pc_config override it). Results are identical for every candidate; only
+ * the time differs. Synchronous. */
+pc_status pc_autotune(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
+                      void* stream, pc_tune_result* out);
+
+/* Set the views rendered by one launch (1..32) for later pc_render calls and
+ * serving groups on this context, replacing the autotuner's choice. 1 gives
+ * one view per launch. */
+pc_status pc_set_views_per_launch(pc_ctx* ctx, uint32_t views_per_launch);
 
 /* ---- timing (per-pass CUDA events) --------------------------------------- */
 

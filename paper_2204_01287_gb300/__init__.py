@@ -24,6 +24,7 @@ _lock = threading.Lock()
 PC_OK, PC_EINVAL, PC_ENOMEM, PC_ENOTFOUND = 0, -1, -2, -3
 PC_EBUSY, PC_ETIMEDOUT, PC_ECUDA, PC_ENOTSUP, PC_EDEVICE = -4, -5, -6, -7, -8
 PC_CFG_TIMING = 1
+PC_CFG_GRAPHS = 2
 PC_VIEW_CULL = 1
 PC_VIEW_NO_EARLY_DEPTH = 2
 EMPTY = 0xFFFFFFFFFFFFFFFF
@@ -84,6 +85,16 @@ class pc_timing(ctypes.Structure):
                 ("raster_launches", ctypes.c_uint64)]
 
 
+class pc_tune_result(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("points_per_warp", ctypes.c_uint32), ("views_per_launch", ctypes.c_uint32),
+                ("ms_per_view", ctypes.c_double), ("ms_per_view_single", ctypes.c_double),
+                ("candidates", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class pc_lod_opts(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_uint32), ("max_node_points", ctypes.c_uint32),
                 ("seed", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
@@ -117,6 +128,8 @@ SIGNATURES = [
     ("pc_render", _i32, [_vp, _u64, _P(pc_view), _u32, _P(pc_framebuffer), _vp]),
     ("pc_render_host", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_vp), _vp]),
     ("pc_get_view_stats", _i32, [_vp, _vp, _u32, _P(pc_view_stats)]),
+    ("pc_autotune", _i32, [_vp, _u64, _P(pc_view), _u32, _vp, _P(pc_tune_result)]),
+    ("pc_set_views_per_launch", _i32, [_vp, _u32]),
     ("pc_timing_begin", _i32, [_vp]),
     ("pc_timing_end", _i32, [_vp, _P(pc_timing)]),
     ("pc_submit", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_u64)]),
@@ -283,6 +296,17 @@ def pc_get_view_stats(ctx: int, view: int = 0, stream: int = 0) -> dict:
     st = pc_view_stats()
     _check(ctx, lib().pc_get_view_stats(ctx, stream, view, ctypes.byref(st)))
     return st.as_dict()
+
+
+def pc_autotune(ctx: int, cloud: int, views, stream: int = 0) -> dict:
+    va = _views_arr(views)
+    r = pc_tune_result()
+    _check(ctx, lib().pc_autotune(ctx, cloud, va, len(views), stream, ctypes.byref(r)))
+    return r.as_dict()
+
+
+def pc_set_views_per_launch(ctx: int, n: int) -> None:
+    _check(ctx, lib().pc_set_views_per_launch(ctx, n))
 
 
 def pc_timing_begin(ctx: int) -> None:

@@ -67,6 +67,7 @@ CloudView Cloud::view() const {
 }
 
 Slot::~Slot() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     cudaFree(scratch.entries);
     cudaFree(scratch.counters);
     cudaFree(scratch.stats);
@@ -124,46 +125,39 @@ std::shared_ptr<Cloud> Ctx::find_cloud(pc_cloud h) {
 }
 
 RasterShape Ctx::shape_for(uint32_t nviews) {
+    const Tune& t = tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
     RasterShape r;
-    r.threads_per_block = cfg.threads_per_block ? (int)cfg.threads_per_block : 256;
+    r.threads_per_block = cfg.threads_per_block ? (int)cfg.threads_per_block
+                          : t.threads_per_block ? t.threads_per_block : 256;
     int per_sm = cfg.blocks_per_sm ? (int)cfg.blocks_per_sm
+                 : t.blocks_per_sm ? t.blocks_per_sm
                                    : raster_occupancy(r.threads_per_block, nviews > 1);
-    if (!cfg.blocks_per_sm && tuned_blocks_per_sm[std::min<uint32_t>(nviews, 32)] > 0)
-        per_sm = tuned_blocks_per_sm[std::min<uint32_t>(nviews, 32)];
     r.blocks = num_sms * per_sm;
     return r;
 }
 
-// Render nviews views with per-view framebuffers on one stream.
-pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
-                      const pc_framebuffer* fbs, cudaStream_t st, Slot* slot) {
-    if (!views || !fbs || nviews == 0 || nviews > kMaxViewsPerRender) {
-        fail_msg("pc_render: need 1..%u views and framebuffers", kMaxViewsPerRender);
-        return PC_EINVAL;
-    }
-    for (uint32_t v = 0; v < nviews; ++v) {
-        const pc_view& pv = views[v];
-        if (pv.width == 0 || pv.height == 0 || pv.width > kMaxDim || pv.height > kMaxDim) {
-            fail_msg("view %u: size %ux%u outside 1..%u", v, pv.width, pv.height, kMaxDim);
-            return PC_EINVAL;
-        }
-        if (!fbs[v].vis || ((uintptr_t)fbs[v].vis & 15) || ((uintptr_t)fbs[v].rgba & 15)) {
-            fail_msg("view %u: framebuffer missing or not 16-byte aligned", v);
-            return PC_EINVAL;
-        }
-    }
-    if (!slot) slot = slot_for(st);
-    std::lock_guard<std::mutex> sg(slot->mu);
-    pc_status rc = ensure_capacity(*slot, cl.n_entries, cl.is_lod ? cl.n_batches : 0);
-    if (rc != PC_OK) return rc;
+uint32_t Ctx::seg_points_for(uint32_t nviews) const {
+    const Tune& t = tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
+    return t.seg_points ? t.seg_points : kSegmentPoints;
+}
+
+uint32_t Ctx::views_per_launch() const {
+    const uint32_t t = tuned_views_per_launch.load();
+    uint32_t v = t ? t : cfg.max_views_per_launch;
+    return std::max<uint32_t>(1, std::min<uint32_t>(v, kMaxViewsPerLaunch));
+}
+
+// The kernels of one frame: per launch group, clear / cull / raster / resolve.
+pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nviews,
+                            const pc_framebuffer* fbs, cudaStream_t st, Slot* slot) {
     const CloudView cv = cl.view();
-    const uint32_t maxv = std::max<uint32_t>(1, std::min<uint32_t>(cfg.max_views_per_launch,
-                                                                    kMaxViewsPerLaunch));
+    const uint32_t maxv = views_per_launch();
     for (uint32_t base = 0; base < nviews; base += maxv) {
         ViewTable vt;
         std::memset(&vt, 0, sizeof vt);
         vt.n = std::min(maxv, nviews - base);
         vt.threshold_px = cfg.precision_px;
+        vt.seg_points = seg_points_for(vt.n);
         for (uint32_t j = 0; j < vt.n; ++j) {
             const pc_view& pv = views[base + j];
             ViewParams& p = vt.v[j];
@@ -198,6 +192,72 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
         launches += 4;
         raster_launches += 1;
     }
+    return PC_OK;
+}
+
+// Render nviews views with per-view framebuffers on one stream. With
+// PC_CFG_GRAPHS (and no per-pass timing) the frame's kernels are captured into
+// a CUDA graph that is updated in place and replayed; a frame with the same
+// launch layout reuses the instantiated graph.
+pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
+                      const pc_framebuffer* fbs, cudaStream_t st, Slot* slot) {
+    if (!views || !fbs || nviews == 0 || nviews > kMaxViewsPerRender) {
+        fail_msg("pc_render: need 1..%u views and framebuffers", kMaxViewsPerRender);
+        return PC_EINVAL;
+    }
+    for (uint32_t v = 0; v < nviews; ++v) {
+        const pc_view& pv = views[v];
+        if (pv.width == 0 || pv.height == 0 || pv.width > kMaxDim || pv.height > kMaxDim) {
+            fail_msg("view %u: size %ux%u outside 1..%u", v, pv.width, pv.height, kMaxDim);
+            return PC_EINVAL;
+        }
+        if (!fbs[v].vis || ((uintptr_t)fbs[v].vis & 15) || ((uintptr_t)fbs[v].rgba & 15)) {
+            fail_msg("view %u: framebuffer missing or not 16-byte aligned", v);
+            return PC_EINVAL;
+        }
+    }
+    if (!slot) slot = slot_for(st);
+    std::lock_guard<std::mutex> sg(slot->mu);
+    pc_status rc = ensure_capacity(*slot, cl.n_entries, cl.is_lod ? cl.n_batches : 0);
+    if (rc != PC_OK) return rc;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    const bool graph = (cfg.flags & PC_CFG_GRAPHS) && !timing_on &&
+                       cs == cudaStreamCaptureStatusNone && st != nullptr;
+    if (graph) {
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    }
+    rc = launch_frame(cl, views, nviews, fbs, st, slot);
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc != PC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        const uint32_t maxv = views_per_launch();
+        const uint64_t key = ((uint64_t)nviews << 8) | maxv | ((uint64_t)cl.is_lod << 40);
+        cudaGraphExec_t& exec = slot->graphs[key];
+        if (exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(exec, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(exec);
+                exec = nullptr;
+            }
+        }
+        if (!exec) e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            exec = nullptr;
+            return cuda_fail(e, "graph instantiate");
+        }
+        e = cudaGraphLaunch(exec, st);
+        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    }
+    if (rc != PC_OK) return rc;
     slot->last_nviews = nviews;
     slot->last_total_batches = cl.n_batches;
     return PC_OK;
@@ -291,7 +351,7 @@ void pc_destroy(pc_ctx* h) {
     cudaDeviceSynchronize();
     for (auto& fe : ctx->frame_events)
         for (auto& ev : fe.ev) cudaEventDestroy(ev);
-    for (auto& kv : ctx->clouds) kv.second->free_device();
+    ctx->clouds.clear();
     ctx->slots.clear();
     delete ctx;
 }
@@ -332,7 +392,7 @@ pc_status pc_upload_encoded(pc_ctx* h, const pc_batch* batches, uint64_t nbatche
             ctx->fail_msg("batch %llu outside the point buffers", (unsigned long long)b);
             return PC_EINVAL;
         }
-        entries += (batches[b].count + kSegmentPoints - 1) / kSegmentPoints;
+        entries += (batches[b].count + kMinSegmentPoints - 1) / kMinSegmentPoints;
     }
     cudaSetDevice(ctx->device);
     auto cl = std::make_shared<Cloud>();
@@ -447,8 +507,7 @@ pc_status pc_release_cloud(pc_ctx* h, pc_cloud cloud) {
         ctx->clouds.erase(it);
     }
     cudaSetDevice(ctx->device);
-    cudaDeviceSynchronize();
-    cl->free_device();
+    cl.reset();   // frees the device buffers unless a queued request still holds them
     return PC_OK;
 }
 

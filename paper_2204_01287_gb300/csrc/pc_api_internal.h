@@ -34,6 +34,10 @@ struct Cloud {
     uint32_t lod_levels = 0;
     void free_device();
     CloudView view() const;
+    // Device memory goes with the last holder (a queued serving request may
+    // still hold the cloud after pc_release_cloud); cudaFree waits for the
+    // device work that uses it.
+    ~Cloud() { free_device(); }
 };
 
 // Scratch and library-owned framebuffers of one stream.
@@ -47,7 +51,15 @@ struct Slot {
     uint64_t host_pixels = 0;
     uint32_t last_nviews = 0;
     uint64_t last_total_batches = 0;
+    std::map<uint64_t, cudaGraphExec_t> graphs;   // replayable frames by launch layout
     ~Slot();
+};
+
+// Launch parameters chosen by pc_autotune, by views per launch.
+struct Tune {
+    int threads_per_block = 0;
+    int blocks_per_sm = 0;
+    uint32_t seg_points = 0;
 };
 
 struct FrameEvents {
@@ -71,7 +83,8 @@ struct Ctx {
     std::deque<FrameEvents> frame_events;
     std::atomic<uint64_t> launches{0};
     std::atomic<uint64_t> raster_launches{0};
-    int tuned_blocks_per_sm[33] = {0};     // autotuner results by views per launch
+    Tune tune[kMaxViewsPerLaunch + 1];      // autotuner results by views per launch
+    std::atomic<uint32_t> tuned_views_per_launch{0};   // 0: cfg.max_views_per_launch
     ServeState* serve = nullptr;
 
     void fail_msg(const char* fmt, ...);
@@ -81,6 +94,10 @@ struct Ctx {
     std::shared_ptr<Cloud> find_cloud(pc_cloud h);
     pc_status ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes);
     RasterShape shape_for(uint32_t nviews);
+    uint32_t seg_points_for(uint32_t nviews) const;
+    uint32_t views_per_launch() const;
+    pc_status launch_frame(const Cloud& cl, const pc_view* views, uint32_t nviews,
+                           const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);
     pc_status render(const Cloud& cl, const pc_view* views, uint32_t nviews,
                      const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);
     pc_status check_device_error(Slot& s);

@@ -13,7 +13,8 @@ namespace pcr {
 
 constexpr uint32_t kMaxViewsPerLaunch = 32;   // views in one raster launch
 constexpr uint32_t kMaxViewsPerRender = 256;  // views in one pc_render call
-constexpr uint32_t kSegmentPoints = 2048;     // points one warp takes per grab
+constexpr uint32_t kSegmentPoints = 2048;     // default points one warp takes per grab
+constexpr uint32_t kMinSegmentPoints = 512;   // smallest grab the draw list is sized for
 constexpr uint32_t kMaxDim = 16384;           // width and height limit
 
 // Counter slots in Scratch::counters.
@@ -59,6 +60,8 @@ struct ViewParams {
 struct ViewTable {
     uint32_t n;
     float threshold_px;   // precision threshold T
+    uint32_t seg_points;  // points per draw-list segment (multiple of 128)
+    uint32_t pad;
     ViewParams v[kMaxViewsPerLaunch];
 };
 static_assert(sizeof(ViewTable) < 4000, "ViewTable must fit the kernel parameter space");

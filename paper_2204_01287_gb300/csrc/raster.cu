@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
             atomicAdd(&sh_stats[v * S_COUNT + S_PK1 + (k - 1)], (unsigned long long)count);
         }
         if (mask) {
-            nseg = (count + kSegmentPoints - 1) / kSegmentPoints;
+            nseg = (count + vt.seg_points - 1) / vt.seg_points;
             uint32_t kl = 0;
             for (uint32_t v = 0; v < vt.n; ++v) kl = max(kl, (uint32_t)((kcodes >> (2 * v)) & 3u));
             atomicAdd(&sh_words, (unsigned long long)kl * count);
@@ -225,8 +225,8 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
         e.kcodes = kcodes;
         e.view_mask = mask;
         e.batch = b;
-        e.seg_first = g * kSegmentPoints;
-        e.seg_count = min(kSegmentPoints, count - g * kSegmentPoints);
+        e.seg_first = g * vt.seg_points;
+        e.seg_count = min(vt.seg_points, count - g * vt.seg_points);
         s.entries[pos] = e;
     }
     __syncthreads();
