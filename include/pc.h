@@ -197,6 +197,30 @@ typedef struct {
 pc_status pc_render(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
                     const pc_framebuffer* fbs, void* stream);
 
+/* Allocation-free variant of the render path (this entry point has no
+ * counterpart in the paper; it exists for callers of this library that must not
+ * allocate device memory: code that runs while another thread captures a CUDA
+ * graph in global mode, where cudaMalloc is refused; plug-ins whose host
+ * application owns every device allocation through its own allocator; render
+ * loops that fix their memory at start-up). It renders one view of an encoded
+ * cloud held in caller-owned device buffers (the pc_encode layout: batches,
+ * w1/w2/w3/color with room for a multiple of 4 words, all 16-byte aligned) into
+ * caller-owned vis and rgba (rgba may be NULL), stream-ordered and
+ * asynchronous, with precision threshold precision_px (512 is the default of
+ * pc_config). It allocates nothing: its scratch (draw list, counters) is a
+ * static device array of about 3 MB that every GPU loading the library holds
+ * until the process exits, so a cloud may have at most
+ * 131,072 - n_points / 2^20 - 1 batches; larger ones get PC_EINVAL, as do
+ * misaligned or missing buffers. The first call on a device looks up that
+ * array's device address (a runtime call, no allocation); make that first
+ * call before any stream capture. All calls share the array and reset its
+ * counters, so calls that overlap on the GPU (different streams, or different
+ * host threads without ordering) race and corrupt each other's results. */
+pc_status pc_render_noalloc(const pc_batch* batches, uint64_t nbatches,
+                            const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                            const uint32_t* color, uint64_t n_points, const pc_view* view,
+                            uint64_t* vis, uint32_t* rgba, float precision_px, void* stream);
+
 /* End-to-end variant: renders into library-owned device framebuffers and
  * copies each view's RGBA image into host_rgba[v] (host, width*height
  * uint32). Returns when the host images are complete. */

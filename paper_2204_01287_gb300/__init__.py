@@ -127,6 +127,8 @@ SIGNATURES = [
     ("pc_build_lod", _i32, [_vp, _u64, _P(pc_lod_opts), _P(_u64)]),
     ("pc_render", _i32, [_vp, _u64, _P(pc_view), _u32, _P(pc_framebuffer), _vp]),
     ("pc_render_host", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_vp), _vp]),
+    ("pc_render_noalloc", _i32, [_vp, _u64, _vp, _vp, _vp, _vp, _u64, _P(pc_view), _vp, _vp,
+                                 ctypes.c_float, _vp]),
     ("pc_get_view_stats", _i32, [_vp, _vp, _u32, _P(pc_view_stats)]),
     ("pc_autotune", _i32, [_vp, _u64, _P(pc_view), _u32, _vp, _P(pc_tune_result)]),
     ("pc_set_views_per_launch", _i32, [_vp, _u32]),
