@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=4000.0,
                     help="Poisson arrival rate of requests per second (offered load)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-lod", action="store_true")
+    ap.add_argument("--lod-points", type=float, default=1e9)
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
 
@@ -261,6 +263,54 @@ def serving_bench(args, pcr, ctx, clouds):
             "identical_bits": hb == hs, "all_ok": batched["ok"] and single["ok"]}
 
 
+def lod_bench(args, pcr, torch, ctx, params):
+    """Sec. 3.5 on the terrain: a layered octree of --lod-points points (max 12
+    levels, <= 10,240 points per node) rendered along the 120-frame fly-through
+    at 1920x1080 with nodes under 300 px culled, against brute force over the
+    same points on the same frames."""
+    import pcsynth
+    n = int(args.lod_points)
+    xyz = np.empty((n, 3), np.float32)
+    rgba = np.empty(n, np.uint32)
+    pcsynth.terrain(n, params, seed=args.seed + 7, out=(xyz, rgba))
+    src = ctx.upload(xyz, rgba)
+    del xyz, rgba
+    t0 = time.perf_counter()
+    lod = pcr.pc_build_lod(ctx.h, src)
+    build_s = time.perf_counter() - t0
+    info = pcr.pc_cloud_get_info(ctx.h, lod)
+    W, H = args.width, args.height
+    frames = [pcsynth.flythrough(params, f, 120, W, H, seed=args.seed) for f in range(120)]
+    fbs = ctx.framebuffers([pcr.make_view(frames[0], W, H)])
+    out = {"points": n, "nodes": info.n_batches, "levels": info.lod_levels, "build_s": build_s,
+           "threshold_px": 300.0, "frames": 120, "resolution": f"{W}x{H}"}
+    for name, cloud, px in (("lod", lod, 300.0), ("brute_force", src, 0.0)):
+        views = [pcr.make_view(m, W, H, pcr.PC_VIEW_CULL, px) for m in frames]
+        for v in views[:3]:
+            ctx.render(cloud, [v], fbs)
+        torch.cuda.synchronize()
+        nodes = pts = 0
+        for v in views[::10]:
+            ctx.render(cloud, [v], fbs)
+            st = ctx.stats()
+            nodes += st["batches_rendered"]
+            pts += st["points_processed"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for v in views:
+            ctx.render(cloud, [v], fbs)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_frame": e0.elapsed_time(e1) / len(views),
+                     "batches_rendered_avg": nodes / len(views[::10]),
+                     "points_processed_avg": pts / len(views[::10])}
+    out["speedup_vs_brute_force"] = out["brute_force"]["ms_per_frame"] / out["lod"]["ms_per_frame"]
+    pcr.pc_release_cloud(ctx.h, lod)
+    pcr.pc_release_cloud(ctx.h, src)
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -423,6 +473,11 @@ def main():
         serving = serving_bench(args, pcr, ctx, clouds)
         log(args, f"serving: {serving}")
 
+    lod = None
+    if not args.no_lod:
+        lod = lod_bench(args, pcr, torch, ctx, params)
+        log(args, f"lod: {lod}")
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         pps, cores, desc, _, _ = cpu_baseline(args, params, m, args.cpu_sample)
@@ -444,7 +499,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "setup_s": {"generate": t_gen, "encode_upload": t_up}},
                 "roofline": roofline, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
-                "serving": serving, "autotune": tune,
+                "serving": serving, "lod": lod, "autotune": tune,
                 "gpu_launches": int(timing.launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -157,12 +157,29 @@ typedef struct {
     uint32_t reserved;
 } pc_lod_opts;
 
-/* Build a layered octree (Sec. 3.5) from a cloud uploaded with pc_upload_cloud:
- * each node is a batch of <= max_node_points points on a cubic box, parents
- * hold uniform subsets of their children's points (additive LOD). Views with
- * lod_px > 0 render only nodes whose projected extent is >= lod_px and whose
- * parent is rendered. *out receives a new cloud; src stays valid. */
+/* Build a layered octree (Sec. 3.5) from a resident cloud: the points are
+ * decoded at full precision (k = 3); the root is the cloud's cubic box; a node
+ * with more than max_node_points points (depth below max_levels - 1) keeps the
+ * max_node_points of smallest priority SplitMix64(seed * 2^32 + index), a
+ * uniform subset, and hands the rest to its octant children (additive: each
+ * point lives in one node). Each node is a batch on its cube, quantized with
+ * Eq. 1 against it. Rendering a LOD cloud draws a node when it is in the
+ * frustum, its projected extent is >= the view's lod_px (the root needs only
+ * the frustum) and its parent is drawn. *out receives a new cloud; src stays. */
 pc_status pc_build_lod(pc_ctx* ctx, pc_cloud src, const pc_lod_opts* opts, pc_cloud* out);
+
+/* Host LOD builder alone (no GPU needed): the tree pc_build_lod uploads, from
+ * host positions xyz (n*3 floats) and colours (may be NULL). Outputs (host,
+ * caller-allocated): up to max_nodes nodes (pc_batch on the node's cube,
+ * breadth-first order), parent[] (root: 0) and level[] per node, and per LOD
+ * point perm (input index), w1/w2/w3 (Eq. 1 against the node cube) and color,
+ * n entries each (every input point lands in exactly one node). *n_nodes gets
+ * the node count; PC_ENOMEM when it exceeds max_nodes (n always suffices). */
+pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
+                        const pc_lod_opts* opts, uint32_t threads, uint64_t max_nodes,
+                        pc_batch* nodes, uint32_t* parent, uint32_t* level, uint64_t* n_nodes,
+                        uint32_t* perm, uint32_t* w1, uint32_t* w2, uint32_t* w3,
+                        uint32_t* color);
 
 /* ---- rendering (Sec. 3.2-3.3, Sec. 3.7) ---------------------------------- */
 

@@ -121,6 +121,17 @@ def lib():
             L.or_render_positions.argtypes = [vp, u64, VP, vp]
             L.or_brute_force.argtypes = [vp, u64, vp, vp, vp, VP, vp]
             L.or_resolve.argtypes = [vp, u64, vp, vp]
+            L.or_decode_cloud.argtypes = [vp, u64, vp, vp, vp, i32, vp]
+            L.or_projected_extent.argtypes = [vp, VP, vp]
+            L.or_projected_extent.restype = i32
+            L.or_splitmix64.argtypes = [u64]
+            L.or_splitmix64.restype = u64
+            L.or_lod_count_nodes.argtypes = [vp, u64, u32, u32, u32]
+            L.or_lod_count_nodes.restype = ctypes.c_int64
+            L.or_lod_build.argtypes = [vp, vp, u64, u32, u32, u32, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.or_lod_build.restype = ctypes.c_int64
+            L.or_lod_select.argtypes = [vp, vp, u64, VP, f32, vp]
+            L.or_lod_render.argtypes = [vp, vp, u64, vp, vp, vp, VP, f32, vp, SP]
             _lib = L
     return _lib
 
@@ -275,3 +286,65 @@ def resolve(vis: np.ndarray, color: np.ndarray):
     out = np.empty(len(vis), np.uint32)
     lib().or_resolve(_p(vis), len(vis), _p(color), _p(out))
     return out
+
+
+# ---- Sec. 3.5 level of detail --------------------------------------------------
+
+def projected_extent(batch, view: View):
+    """Projected extent in pixels, or None when a corner has w <= 0."""
+    e = np.zeros(1, np.float32)
+    ok = lib().or_projected_extent(_p(_batch_arr(batch)), ctypes.byref(view), _p(e))
+    return float(e[0]) if ok else None
+
+
+def splitmix64(z: int) -> int:
+    return lib().or_splitmix64(int(z) & 0xFFFFFFFFFFFFFFFF)
+
+
+class LodCloud:
+    """Oracle layered octree: nodes (batches), parent, level, words, colours
+    and perm (LOD point -> input index)."""
+
+    def __init__(self, nodes, parent, level, w1, w2, w3, color, perm):
+        self.nodes, self.parent, self.level = nodes, parent, level
+        self.w1, self.w2, self.w3, self.color, self.perm = w1, w2, w3, color, perm
+
+
+def lod_build(xyz, rgba, max_levels=12, max_node_points=10240, seed=0) -> LodCloud:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    rgba = np.ascontiguousarray(rgba, np.uint32)
+    n = len(xyz)
+    nn = lib().or_lod_count_nodes(_p(xyz), n, max_levels, max_node_points, seed)
+    nodes = np.zeros(max(nn, 1), BATCH_DTYPE)
+    parent = np.zeros(max(nn, 1), np.uint32)
+    level = np.zeros(max(nn, 1), np.uint32)
+    w = [np.zeros(max(n, 1), np.uint32) for _ in range(5)]
+    got = lib().or_lod_build(_p(xyz), _p(rgba), n, max_levels, max_node_points, seed,
+                             _p(nodes), _p(parent), _p(level), _p(w[4]), _p(w[0]), _p(w[1]),
+                             _p(w[2]), _p(w[3]))
+    assert got == nn
+    return LodCloud(nodes[:nn], parent[:nn], level[:nn], w[0][:n], w[1][:n], w[2][:n],
+                    w[3][:n], w[4][:n])
+
+
+def lod_select(lod: LodCloud, view: View, lod_px: float):
+    sel = np.zeros(max(len(lod.nodes), 1), np.uint8)
+    lib().or_lod_select(_p(lod.nodes), _p(lod.parent), len(lod.nodes), ctypes.byref(view),
+                        float(lod_px), _p(sel))
+    return sel[:len(lod.nodes)]
+
+
+def lod_render(lod: LodCloud, view: View, lod_px: float):
+    vis = np.empty(view.width * view.height, np.uint64)
+    st = Stats()
+    lib().or_lod_render(_p(lod.nodes), _p(lod.parent), len(lod.nodes), _p(lod.w1), _p(lod.w2),
+                        _p(lod.w3), ctypes.byref(view), float(lod_px), _p(vis), ctypes.byref(st))
+    return vis, st.as_dict()
+
+
+def decode_cloud(enc: Encoded, k: int = 3) -> np.ndarray:
+    """Decoded positions of every point of an encoded cloud at precision k."""
+    out = np.zeros((max(enc.n, 1), 3), np.float32)
+    lib().or_decode_cloud(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2),
+                          _p(enc.w3), int(k), _p(out))
+    return out[:enc.n]

@@ -172,6 +172,15 @@ void or_decode_position(const or_batch* b, int k, uint32_t w1, uint32_t w2,
     }
 }
 
+void or_decode_cloud(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                     const uint32_t* w2, const uint32_t* w3, int k, float* xyz) {
+    for (uint64_t b = 0; b < nbatches; ++b)
+        for (uint32_t j = 0; j < batches[b].count; ++j) {
+            uint64_t i = (uint64_t)batches[b].first + j;
+            or_decode_position(&batches[b], k, w1[i], w2[i], w3[i], &xyz[3 * i]);
+        }
+}
+
 int or_project_position(const float p[3], const or_view* v, uint32_t idx,
                         uint32_t* pixel, uint64_t* key, float fxy[2]) {
     const float* m = v->m;
@@ -422,4 +431,233 @@ void or_resolve(const uint64_t* vis, uint64_t npixels, const uint32_t* color,
                 uint32_t* out) {
     for (uint64_t p = 0; p < npixels; ++p)
         out[p] = vis[p] == OR_EMPTY ? 0u : color[(uint32_t)(vis[p] & 0xFFFFFFFFull)];
+}
+
+/* ---- Sec. 3.5 level of detail --------------------------------------------- */
+
+int or_projected_extent(const or_batch* b, const or_view* v, float* extent) {
+    float fmin[2] = {0, 0}, fmax[2] = {0, 0};
+    for (int c = 0; c < 8; ++c) {
+        float p[3];
+        for (int a = 0; a < 3; ++a)
+            p[a] = ((c >> a) & 1) ? b->min[a] + b->size[a] : b->min[a];
+        const float* m = v->m;
+        float cw = ((m[3] * p[0] + m[7] * p[1]) + m[11] * p[2]) + m[15];
+        if (!(cw > 0.0f)) return 0;
+        float f[2];
+        uint32_t pix;
+        uint64_t key;
+        or_project_position(p, v, 0, &pix, &key, f);
+        for (int a = 0; a < 2; ++a) {
+            if (c == 0 || f[a] < fmin[a]) fmin[a] = f[a];
+            if (c == 0 || f[a] > fmax[a]) fmax[a] = f[a];
+        }
+    }
+    float ex = fmax[0] - fmin[0];
+    float ey = fmax[1] - fmin[1];
+    if (ex != ex || ey != ey) *extent = ex + ey;   /* NaN: never below a threshold */
+    else *extent = ex > ey ? ex : ey;
+    return 1;
+}
+
+uint64_t or_splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+typedef struct {
+    float lo[3];
+    float size;
+    uint32_t level;
+    uint32_t parent;
+    uint32_t* idx;      /* input indices of the node's points and its subtree */
+    uint64_t n;
+} lod_work;
+
+typedef struct { uint64_t pri; uint32_t idx; } lod_pri;
+
+static int lod_pri_cmp(const void* a, const void* b) {
+    const lod_pri* x = (const lod_pri*)a;
+    const lod_pri* y = (const lod_pri*)b;
+    if (x->pri != y->pri) return x->pri < y->pri ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static int u32_cmp(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return x < y ? -1 : (x > y);
+}
+
+/* Builds the tree breadth first. When out_nodes is NULL only counts nodes. */
+static int64_t lod_build_impl(const float* xyz, const uint32_t* rgba, uint64_t n,
+                              uint32_t max_levels, uint32_t max_node_points, uint32_t seed,
+                              or_batch* nodes, uint32_t* parent, uint32_t* level, uint32_t* perm,
+                              uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color) {
+    if (n == 0 || max_levels == 0 || max_node_points == 0) return 0;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = xyz[a];
+    for (uint64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (xyz[3 * i + a] < lo[a]) lo[a] = xyz[3 * i + a];
+            if (xyz[3 * i + a] > hi[a]) hi[a] = xyz[3 * i + a];
+        }
+    float side = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        float e = hi[a] - lo[a];
+        if (e > side) side = e;
+    }
+    /* breadth-first queue of work items */
+    uint64_t cap = 1024, head = 0, tail = 0;
+    lod_work* q = (lod_work*)malloc(sizeof(lod_work) * cap);
+    uint32_t* all = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    for (uint64_t i = 0; i < n; ++i) all[i] = (uint32_t)i;
+    q[tail].lo[0] = lo[0]; q[tail].lo[1] = lo[1]; q[tail].lo[2] = lo[2];
+    q[tail].size = side; q[tail].level = 0; q[tail].parent = 0;
+    q[tail].idx = all; q[tail].n = n;
+    ++tail;
+    uint64_t out_pts = 0;
+    int64_t id = 0;
+    while (head < tail) {
+        lod_work w = q[head++];
+        uint64_t keep = w.n;
+        uint32_t* kept = w.idx;            /* the node's own points, input order */
+        uint32_t* rest = NULL;
+        uint64_t nrest = 0;
+        if (w.n > max_node_points && w.level + 1 < max_levels) {
+            lod_pri* pr = (lod_pri*)malloc(sizeof(lod_pri) * w.n);
+            for (uint64_t j = 0; j < w.n; ++j) {
+                pr[j].idx = w.idx[j];
+                pr[j].pri = or_splitmix64(((uint64_t)seed << 32) + w.idx[j]);
+            }
+            qsort(pr, w.n, sizeof(lod_pri), lod_pri_cmp);
+            keep = max_node_points;
+            kept = (uint32_t*)malloc(sizeof(uint32_t) * keep);
+            rest = (uint32_t*)malloc(sizeof(uint32_t) * (w.n - keep));
+            for (uint64_t j = 0; j < keep; ++j) kept[j] = pr[j].idx;
+            for (uint64_t j = keep; j < w.n; ++j) rest[nrest++] = pr[j].idx;
+            free(pr);
+            qsort(kept, keep, sizeof(uint32_t), u32_cmp);   /* input order */
+            qsort(rest, nrest, sizeof(uint32_t), u32_cmp);
+        }
+        if (nodes) {
+            or_batch* B = &nodes[id];
+            for (int a = 0; a < 3; ++a) { B->min[a] = w.lo[a]; B->size[a] = w.size; }
+            B->first = (uint32_t)out_pts;
+            B->count = (uint32_t)keep;
+            parent[id] = w.parent;
+            level[id] = w.level;
+            for (uint64_t j = 0; j < keep; ++j) {
+                const float* p = &xyz[3 * (uint64_t)kept[j]];
+                uint32_t X = or_quantize30(p[0], B->min[0], B->size[0]);
+                uint32_t Y = or_quantize30(p[1], B->min[1], B->size[1]);
+                uint32_t Z = or_quantize30(p[2], B->min[2], B->size[2]);
+                uint32_t ws[3];
+                or_split_words(X, Y, Z, ws);
+                perm[out_pts + j] = kept[j];
+                w1[out_pts + j] = ws[0];
+                w2[out_pts + j] = ws[1];
+                w3[out_pts + j] = ws[2];
+                color[out_pts + j] = rgba ? rgba[kept[j]] : 0u;
+            }
+        }
+        out_pts += keep;
+        if (nrest) {
+            /* octant of each remaining point against the cube's midpoints */
+            float half = w.size * 0.5f;
+            float mid[3];
+            for (int a = 0; a < 3; ++a) mid[a] = w.lo[a] + half;
+            for (int o = 0; o < 8; ++o) {
+                uint64_t cnt = 0;
+                for (uint64_t j = 0; j < nrest; ++j) {
+                    const float* p = &xyz[3 * (uint64_t)rest[j]];
+                    int oct = (p[0] >= mid[0]) | ((p[1] >= mid[1]) << 1) | ((p[2] >= mid[2]) << 2);
+                    if (oct == o) ++cnt;
+                }
+                if (!cnt) continue;
+                uint32_t* ci = (uint32_t*)malloc(sizeof(uint32_t) * cnt);
+                uint64_t k = 0;
+                for (uint64_t j = 0; j < nrest; ++j) {
+                    const float* p = &xyz[3 * (uint64_t)rest[j]];
+                    int oct = (p[0] >= mid[0]) | ((p[1] >= mid[1]) << 1) | ((p[2] >= mid[2]) << 2);
+                    if (oct == o) ci[k++] = rest[j];
+                }
+                if (tail == cap) {
+                    cap *= 2;
+                    q = (lod_work*)realloc(q, sizeof(lod_work) * cap);
+                }
+                lod_work* c = &q[tail++];
+                for (int a = 0; a < 3; ++a) c->lo[a] = ((o >> a) & 1) ? mid[a] : w.lo[a];
+                c->size = half;
+                c->level = w.level + 1;
+                c->parent = (uint32_t)id;
+                c->idx = ci;
+                c->n = cnt;
+            }
+            free(rest);
+        }
+        if (kept != w.idx) free(kept);
+        free(w.idx);
+        ++id;
+    }
+    free(q);
+    return id;
+}
+
+int64_t or_lod_count_nodes(const float* xyz, uint64_t n, uint32_t max_levels,
+                           uint32_t max_node_points, uint32_t seed) {
+    return lod_build_impl(xyz, NULL, n, max_levels, max_node_points, seed, NULL, NULL, NULL,
+                          NULL, NULL, NULL, NULL, NULL);
+}
+
+int64_t or_lod_build(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t max_levels,
+                     uint32_t max_node_points, uint32_t seed, or_batch* nodes,
+                     uint32_t* parent, uint32_t* level, uint32_t* perm, uint32_t* w1,
+                     uint32_t* w2, uint32_t* w3, uint32_t* color) {
+    return lod_build_impl(xyz, rgba, n, max_levels, max_node_points, seed, nodes, parent, level,
+                          perm, w1, w2, w3, color);
+}
+
+void or_lod_select(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
+                   const or_view* v, float lod_px, uint8_t* sel) {
+    for (uint64_t i = 0; i < nnodes; ++i) {
+        int ok = !or_cull(&nodes[i], v);
+        if (ok && i > 0) {
+            float e;
+            if (or_projected_extent(&nodes[i], v, &e)) ok = !(e < lod_px);
+        }
+        if (ok && i > 0) ok = sel[parent[i]];
+        sel[i] = (uint8_t)ok;
+    }
+}
+
+void or_lod_render(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
+                   const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                   const or_view* v, float lod_px, uint64_t* vis, or_stats* st) {
+    uint64_t npix = (uint64_t)v->width * v->height;
+    for (uint64_t p = 0; p < npix; ++p) vis[p] = OR_EMPTY;
+    if (st) memset(st, 0, sizeof(*st));
+    uint8_t* sel = (uint8_t*)malloc(nnodes ? nnodes : 1);
+    or_lod_select(nodes, parent, nnodes, v, lod_px, sel);
+    for (uint64_t i = 0; i < nnodes; ++i) {
+        if (!sel[i]) continue;
+        const or_batch* b = &nodes[i];
+        int k = or_select_k(b, v);
+        if (st) {
+            st->batches_rendered += 1;
+            st->points_processed += b->count;
+            st->batches_k[k] += 1;
+            st->points_k[k] += b->count;
+        }
+        for (uint32_t j = 0; j < b->count; ++j) {
+            uint32_t idx = b->first + j;
+            uint32_t pix;
+            uint64_t key;
+            if (!or_project_point(b, k, w1[idx], w2[idx], w3[idx], idx, v, &pix, &key)) continue;
+            if (st) st->points_accepted += 1;
+            if (key < vis[pix]) vis[pix] = key;
+        }
+    }
+    free(sel);
 }

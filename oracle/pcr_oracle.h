@@ -91,6 +91,10 @@ void or_decode_position(const or_batch* b, int k, uint32_t w1, uint32_t w2,
 /* Sec. 3.3: precision of a batch in a view, from its projected extent. */
 int or_select_k(const or_batch* b, const or_view* v);
 
+/* Decoded positions of every point of an encoded cloud at precision k. */
+void or_decode_cloud(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                     const uint32_t* w2, const uint32_t* w3, int k, float* xyz);
+
 /* Sec. 3.2: 1 if no point of the batch can land in the viewport. */
 int or_cull(const or_batch* b, const or_view* v);
 
@@ -114,6 +118,47 @@ void or_render_positions(const float* xyz, uint64_t n, const or_view* v, uint64_
 void or_brute_force(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
                     const uint32_t* w2, const uint32_t* w3, const or_view* v,
                     uint64_t* vis);
+
+/* ---- Sec. 3.5 level of detail ------------------------------------------- */
+
+/* Projected extent of a batch box in a view: max over x and y of the spread
+ * of the 8 corners' unfloored pixel coordinates (the same binary32 operations
+ * as a point). Returns 0 and leaves *extent unset when a corner has w <= 0. */
+int or_projected_extent(const or_batch* b, const or_view* v, float* extent);
+
+/* SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014). */
+uint64_t or_splitmix64(uint64_t z);
+
+/* Number of LOD nodes or_lod_build would create (first pass), or -1. */
+int64_t or_lod_count_nodes(const float* xyz, uint64_t n, uint32_t max_levels,
+                           uint32_t max_node_points, uint32_t seed);
+
+/* Sec. 3.5 layered octree, additive: the root is the cubic box of the cloud;
+ * a node with more than max_node_points points (and depth below max_levels-1)
+ * keeps the max_node_points points of smallest priority SplitMix64(seed*2^32 +
+ * index) (a uniform subset; ties by index) and hands the rest to its 8 octant
+ * children; other nodes keep all their points. Nodes are numbered breadth
+ * first, children in octant order (bit 0 = x upper half, bit 1 = y, bit 2 = z).
+ * Each node is one batch on its cubic box (min = cube corner, size = cube side
+ * on all axes) whose points (in input order) are quantized with Eq. 1 against
+ * that box. perm[j] = input index of LOD point j. Returns the number of nodes. */
+int64_t or_lod_build(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t max_levels,
+                     uint32_t max_node_points, uint32_t seed, or_batch* nodes,
+                     uint32_t* parent, uint32_t* level, uint32_t* perm, uint32_t* w1,
+                     uint32_t* w2, uint32_t* w3, uint32_t* color);
+
+/* Sec. 3.5 node selection: node n is drawn when it is in the frustum (the
+ * culling test of Sec. 3.2), its projected extent is at least lod_px (any
+ * corner with w <= 0 counts as large; the root needs only the frustum test),
+ * and its parent is drawn. sel[n] = 1 for drawn nodes. Nodes must be in
+ * breadth-first order (parents first). */
+void or_lod_select(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
+                   const or_view* v, float lod_px, uint8_t* sel);
+
+/* Geometry pass over the drawn nodes of a LOD cloud. */
+void or_lod_render(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
+                   const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                   const or_view* v, float lod_px, uint64_t* vis, or_stats* st);
 
 /* Sec. 3.3 visibility buffer: out[p] = colour of the winning point, 0 where
  * no point landed. */

@@ -125,6 +125,8 @@ SIGNATURES = [
     ("pc_cloud_download", _i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     ("pc_release_cloud", _i32, [_vp, _u64]),
     ("pc_build_lod", _i32, [_vp, _u64, _P(pc_lod_opts), _P(_u64)]),
+    ("pc_lod_encode", _i32, [_vp, _vp, _u64, _P(pc_lod_opts), _u32, _u64, _vp, _vp, _vp,
+                             _P(_u64), _vp, _vp, _vp, _vp, _vp]),
     ("pc_render", _i32, [_vp, _u64, _P(pc_view), _u32, _P(pc_framebuffer), _vp]),
     ("pc_render_host", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_vp), _vp]),
     ("pc_render_noalloc", _i32, [_vp, _u64, _vp, _vp, _vp, _vp, _u64, _P(pc_view), _vp, _vp,
@@ -260,6 +262,26 @@ def pc_build_lod(ctx: int, cloud: int, max_levels: int = 12, max_node_points: in
     out = ctypes.c_uint64()
     _check(ctx, lib().pc_build_lod(ctx, cloud, ctypes.byref(o), ctypes.byref(out)))
     return out.value
+
+
+def pc_lod_encode(xyz: np.ndarray, rgba, max_levels: int = 12, max_node_points: int = 10240,
+                  seed: int = 0, threads: int = 0):
+    """Host LOD builder: (nodes, parent, level, perm, w1, w2, w3, color)."""
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    n = xyz.shape[0]
+    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    cap = max(n, 1)
+    nodes = np.zeros(cap, BATCH_DTYPE)
+    parent = np.zeros(cap, np.uint32)
+    level = np.zeros(cap, np.uint32)
+    nn = ctypes.c_uint64()
+    w = [np.zeros(max(n, 1), np.uint32) for _ in range(5)]
+    o = pc_lod_opts(max_levels, max_node_points, seed, 0)
+    _check(None, lib().pc_lod_encode(_np_ptr(xyz), _np_ptr(rgba), n, ctypes.byref(o), threads,
+                                     cap, _np_ptr(nodes), _np_ptr(parent), _np_ptr(level),
+                                     ctypes.byref(nn), *(x.ctypes.data for x in w)))
+    k = nn.value
+    return nodes[:k], parent[:k], level[:k], w[0][:n], w[1][:n], w[2][:n], w[3][:n], w[4][:n]
 
 
 def make_view(m, width: int, height: int, flags: int = 0, lod_px: float = 0.0) -> pc_view:

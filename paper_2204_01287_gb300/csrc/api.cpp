@@ -100,7 +100,7 @@ pc_status Ctx::ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes) {
         cudaFree(s.scratch.lod_sel);
         s.scratch.lod_sel = nullptr;
         s.lod_capacity = 0;
-        cudaError_t e = cudaMalloc(&s.scratch.lod_sel, nodes);
+        cudaError_t e = cudaMalloc(&s.scratch.lod_sel, nodes * sizeof(uint32_t));
         if (e != cudaSuccess) return cuda_fail(e, "lod selection");
         s.lod_capacity = nodes;
     }
@@ -180,6 +180,11 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
         cudaError_t e = launch_clear(vt, base, slot->scratch, st);
         if (e != cudaSuccess) return cuda_fail(e, "clear launch");
         if (fe) cudaEventRecord(fe->ev[1], st);
+        if (cl.is_lod) {
+            e = launch_lod_pass(cv, vt, slot->scratch, st);
+            if (e != cudaSuccess) return cuda_fail(e, "LOD selection launch");
+            launches += 1;
+        }
         e = launch_cull(cv, vt, base, slot->scratch, st);
         if (e != cudaSuccess) return cuda_fail(e, "cull launch");
         if (fe) cudaEventRecord(fe->ev[2], st);
@@ -375,12 +380,23 @@ pc_status pc_encode(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t
     }
 }
 
-pc_status pc_upload_encoded(pc_ctx* h, const pc_batch* batches, uint64_t nbatches,
-                            const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
-                            const uint32_t* color, uint64_t n, pc_cloud* out) {
-    if (!h || !out) return PC_EINVAL;
-    Ctx* ctx = reinterpret_cast<Ctx*>(h);
-    *out = 0;
+}  // extern "C"
+
+namespace pcr {
+
+pc_cloud Ctx::register_cloud(const std::shared_ptr<Cloud>& cl) {
+    std::lock_guard<std::mutex> g(mu);
+    pc_cloud handle = ++next_handle;
+    clouds[handle] = cl;
+    return handle;
+}
+
+// Copy an encoded cloud to library-owned device memory (no handle yet).
+pc_status upload_encoded_internal(Ctx& c, const pc_batch* batches, uint64_t nbatches,
+                                  const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                                  const uint32_t* color, uint64_t n,
+                                  std::shared_ptr<Cloud>& out) {
+    Ctx* ctx = &c;
     if (n >= 0xFFFFFFFFull || nbatches >= 0xFFFFFFFFull) {
         ctx->fail_msg("cloud too large: %llu points", (unsigned long long)n);
         return PC_EINVAL;
@@ -424,10 +440,26 @@ pc_status pc_upload_encoded(pc_ctx* h, const pc_batch* batches, uint64_t nbatche
         return ctx->cuda_fail(e, "cloud upload");
     }
     cl->device_bytes = 4 * wb + nbatches * sizeof(pc_batch);
-    std::lock_guard<std::mutex> g(ctx->mu);
-    pc_cloud handle = ++ctx->next_handle;
-    ctx->clouds[handle] = cl;
-    *out = handle;
+    out = cl;
+    return PC_OK;
+}
+
+}  // namespace pcr
+
+extern "C" {
+
+
+
+pc_status pc_upload_encoded(pc_ctx* h, const pc_batch* batches, uint64_t nbatches,
+                            const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                            const uint32_t* color, uint64_t n, pc_cloud* out) {
+    if (!h || !out) return PC_EINVAL;
+    Ctx* ctx = reinterpret_cast<Ctx*>(h);
+    *out = 0;
+    std::shared_ptr<Cloud> cl;
+    pc_status rc = upload_encoded_internal(*ctx, batches, nbatches, w1, w2, w3, color, n, cl);
+    if (rc != PC_OK) return rc;
+    *out = ctx->register_cloud(cl);
     return PC_OK;
 }
 

@@ -45,7 +45,7 @@ struct Slot {
     cudaStream_t stream = nullptr;
     std::mutex mu;
     Scratch scratch{};
-    uint64_t lod_capacity = 0;
+    uint64_t lod_capacity = 0;      // nodes the LOD selection buffer holds
     uint64_t* host_vis = nullptr;     // pc_render_host framebuffers
     uint32_t* host_rgba = nullptr;
     uint64_t host_pixels = 0;
@@ -101,7 +101,19 @@ struct Ctx {
     pc_status render(const Cloud& cl, const pc_view* views, uint32_t nviews,
                      const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);
     pc_status check_device_error(Slot& s);
+    pc_cloud register_cloud(const std::shared_ptr<Cloud>& cl);
 };
+
+pc_status upload_encoded_internal(Ctx& ctx, const pc_batch* batches, uint64_t nbatches,
+                                  const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                                  const uint32_t* color, uint64_t n,
+                                  std::shared_ptr<Cloud>& out);
+
+pc_status lod_encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
+                          uint32_t max_levels, uint32_t M, uint32_t seed, unsigned threads,
+                          std::vector<pc_batch>& nodes, std::vector<uint32_t>& parent,
+                          std::vector<uint32_t>& level, uint32_t* perm, uint32_t* w1,
+                          uint32_t* w2, uint32_t* w3, uint32_t* color);
 
 // serve.cpp
 void serve_shutdown(Ctx& ctx);

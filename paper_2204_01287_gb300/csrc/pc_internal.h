@@ -96,7 +96,7 @@ struct Scratch {
     uint64_t capacity;    // entries
     uint32_t* counters;   // C_COUNT
     unsigned long long* stats;  // kMaxViewsPerRender * S_COUNT
-    uint8_t* lod_sel;     // LOD: per node and view group, selected flag (n_batches)
+    uint32_t* lod_sel;    // LOD: per node, bit v = node passes view v of the launch
 };
 
 // Launch-shape knobs for the raster kernel.
@@ -111,6 +111,8 @@ cudaError_t launch_clear(const ViewTable& vt, uint32_t view_base, Scratch s,
                          cudaStream_t st);
 cudaError_t launch_cull(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                         Scratch s, cudaStream_t st);
+// LOD clouds: per node, the views whose frustum and size tests it passes.
+cudaError_t launch_lod_pass(const CloudView& c, const ViewTable& vt, Scratch s, cudaStream_t st);
 cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                           Scratch s, RasterShape shape, cudaStream_t st);
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s,

@@ -75,11 +75,9 @@ __device__ __forceinline__ float to_pixel(float c, float w, float W) {
     return __fmul_rn(__fadd_rn(__fmul_rn(__fdiv_rn(c, w), 0.5f), 0.5f), W);
 }
 
-// Sec. 3.3: smallest k whose cells are below the threshold, from the extent
-// of the 8 projected box corners; 3 when a corner is not in front of the eye.
-__device__ int select_k(const pc_batch& b, const ViewParams& v, float T) {
-    const uint32_t fk = (v.flags & PC_VIEW_K_MASK) >> 4;
-    if (fk >= 1) return (int)fk;
+// Spread of the 8 projected box corners' unfloored pixel coordinates, with
+// the same binary32 operations as a point; false when a corner has w <= 0.
+__device__ bool corner_extent(const pc_batch& b, const ViewParams& v, float& ex, float& ey) {
     float hi[3];
     for (int a = 0; a < 3; ++a) hi[a] = __fadd_rn(b.min[a], b.size[a]);
     float fmin0 = 0.f, fmax0 = 0.f, fmin1 = 0.f, fmax1 = 0.f;
@@ -90,7 +88,7 @@ __device__ int select_k(const pc_batch& b, const ViewParams& v, float T) {
         float y = (c & 2) ? hi[1] : b.min[1];
         float z = (c & 4) ? hi[2] : b.min[2];
         float cw = clip_row(v.m, 3, x, y, z);
-        if (!(cw > 0.0f)) return 3;
+        if (!(cw > 0.0f)) return false;
         float f0 = to_pixel(clip_row(v.m, 0, x, y, z), cw, W);
         float f1 = to_pixel(clip_row(v.m, 1, x, y, z), cw, H);
         if (c == 0 || f0 < fmin0) fmin0 = f0;
@@ -98,7 +96,18 @@ __device__ int select_k(const pc_batch& b, const ViewParams& v, float T) {
         if (c == 0 || f1 < fmin1) fmin1 = f1;
         if (c == 0 || f1 > fmax1) fmax1 = f1;
     }
-    const float ex = __fsub_rn(fmax0, fmin0), ey = __fsub_rn(fmax1, fmin1);
+    ex = __fsub_rn(fmax0, fmin0);
+    ey = __fsub_rn(fmax1, fmin1);
+    return true;
+}
+
+// Sec. 3.3: smallest k whose cells are below the threshold, from the extent
+// of the 8 projected box corners; 3 when a corner is not in front of the eye.
+__device__ int select_k(const pc_batch& b, const ViewParams& v, float T) {
+    const uint32_t fk = (v.flags & PC_VIEW_K_MASK) >> 4;
+    if (fk >= 1) return (int)fk;
+    float ex, ey;
+    if (!corner_extent(b, v, ex, ey)) return 3;
     if (ex < T && ey < T) return 1;
     const float T2 = __fmul_rn(T, 1024.0f);
     if (ex < T2 && ey < T2) return 2;
@@ -168,6 +177,29 @@ __device__ bool cull_batch(const pc_batch& b, const ViewParams& v) {
 
 constexpr int kCullThreads = 128;
 
+// Sec. 3.5: a node passes a view when it is in the frustum and, unless it is
+// the root, its projected extent reaches the view's threshold (a corner with
+// w <= 0 counts as large). lod_sel[n] gets one bit per view of the launch.
+__global__ void __launch_bounds__(kCullThreads) k_lod_pass(CloudView c, ViewTable vt, Scratch s) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= c.n_batches) return;
+    const pc_batch bt = c.batches[n];
+    uint32_t mask = 0;
+    for (uint32_t v = 0; v < vt.n; ++v) {
+        const ViewParams& vp = vt.v[v];
+        if (cull_batch(bt, vp)) continue;
+        if (n > 0) {
+            float ex, ey;
+            if (corner_extent(bt, vp, ex, ey)) {
+                const float e = (ex != ex || ey != ey) ? __fadd_rn(ex, ey) : fmaxf(ex, ey);
+                if (e < vp.lod_px) continue;
+            }
+        }
+        mask |= 1u << v;
+    }
+    s.lod_sel[n] = mask;
+}
+
 __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt, uint32_t view_base,
                                                      Scratch s) {
     __shared__ unsigned long long sh_stats[kMaxViewsPerLaunch * S_COUNT];
@@ -186,9 +218,26 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
             raise_error(s, E_BATCH_RANGE, b);
             count = 0;
         }
+        uint32_t lod_mask = ~0u;
+        if (c.is_lod) {
+            // drawn when this node and every ancestor passed (parents come
+            // first in breadth-first order; the root is its own parent)
+            lod_mask = s.lod_sel[b];
+            uint32_t node = b;
+            for (int depth = 0; depth < 64 && lod_mask; ++depth) {
+                const uint32_t par = c.parent[node];
+                if (par == node || par >= c.n_batches) break;
+                lod_mask &= s.lod_sel[par];
+                node = par;
+            }
+        }
         for (uint32_t v = 0; v < vt.n && count; ++v) {
             const ViewParams& vp = vt.v[v];
-            if ((vp.flags & PC_VIEW_CULL) && cull_batch(bt, vp)) continue;
+            if (c.is_lod) {
+                if (!((lod_mask >> v) & 1u)) continue;
+            } else if ((vp.flags & PC_VIEW_CULL) && cull_batch(bt, vp)) {
+                continue;
+            }
             const int k = select_k(bt, vp, vt.threshold_px);
             mask |= 1u << v;
             kcodes |= (uint64_t)k << (2 * v);
@@ -594,6 +643,13 @@ cudaError_t launch_clear(const ViewTable& vt, uint32_t view_base, Scratch s, cud
     blocks = blocks < 1 ? 1 : (blocks > (uint64_t)num_sms() * 8 ? (uint64_t)num_sms() * 8 : blocks);
     dim3 grid((unsigned)blocks, vt.n ? vt.n : 1);
     k_clear<<<grid, threads, 0, st>>>(vt, view_base, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lod_pass(const CloudView& c, const ViewTable& vt, Scratch s, cudaStream_t st) {
+    const unsigned blocks = (c.n_batches + kCullThreads - 1) / kCullThreads;
+    if (blocks == 0) return cudaSuccess;
+    k_lod_pass<<<blocks, kCullThreads, 0, st>>>(c, vt, s);
     return cudaGetLastError();
 }
 

@@ -422,6 +422,4 @@ pc_status pc_release_ticket(pc_ctx* h, pc_ticket ticket) {
     return PC_OK;
 }
 
-pc_status pc_build_lod(pc_ctx*, pc_cloud, const pc_lod_opts*, pc_cloud*) { return PC_ENOTSUP; }
-
 }  // extern "C"

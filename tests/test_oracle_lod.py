@@ -1,0 +1,162 @@
+"""Pins of the oracle's level-of-detail structure and node selection (Sec. 3.5)
+against properties that define them: an additive layered octree holds every
+point exactly once, nodes are cubic octants of their parent, a parent keeps the
+max_node_points points of smallest priority among its subtree, points are
+quantized with Eq. 1 against their node's cube, and selection draws a node
+only when it is in the frustum, big enough on screen and its parent is drawn.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import pcsynth as S
+
+M, L, SEED = 1024, 12, 7
+
+
+@pytest.fixture(scope="module")
+def lod():
+    p = S.terrain_params(3000.0, 0.15, 80)
+    xyz, rgba = S.terrain(60000, p, seed=11)
+    return p, xyz, rgba, O.lod_build(xyz, rgba, L, M, SEED)
+
+
+def _children(lod):
+    ch = {i: [] for i in range(len(lod.nodes))}
+    for i in range(1, len(lod.nodes)):
+        ch[int(lod.parent[i])].append(i)
+    return ch
+
+
+def test_every_point_exactly_once(lod):
+    _, xyz, rgba, t = lod
+    assert np.array_equal(np.sort(t.perm), np.arange(len(xyz), dtype=np.uint32))
+    assert np.array_equal(t.color, rgba[t.perm])
+    firsts = t.nodes["first"].astype(np.int64)
+    counts = t.nodes["count"].astype(np.int64)
+    assert firsts[0] == 0 and np.array_equal(firsts[1:], np.cumsum(counts)[:-1])
+    assert counts.sum() == len(xyz)
+
+
+def test_tree_shape(lod):
+    _, xyz, _, t = lod
+    ch = _children(t)
+    assert t.level[0] == 0 and t.parent[0] == 0
+    for i in range(1, len(t.nodes)):
+        par = int(t.parent[i])
+        assert par < i and t.level[i] == t.level[par] + 1          # breadth first
+        assert t.level[i] >= t.level[i - 1]
+        half = np.float32(t.nodes[par]["size"][0] * np.float32(0.5))
+        assert np.all(t.nodes[i]["size"] == half)
+        lo_p = t.nodes[par]["min"]
+        mid = (lo_p + half).astype(np.float32)
+        lo_c = t.nodes[i]["min"]
+        assert all(lo_c[a] in (lo_p[a], mid[a]) for a in range(3))
+    for i, cs in ch.items():
+        octs = [int(sum((t.nodes[c]["min"][a] != t.nodes[i]["min"][a]) << a for a in range(3)))
+                for c in cs]
+        assert octs == sorted(octs) and len(set(octs)) == len(octs)
+        if cs:
+            assert t.nodes[i]["count"] == M                     # full parents
+        else:
+            assert t.nodes[i]["count"] <= M or t.level[i] == L - 1
+    assert len(t.nodes) > 20 and t.level.max() >= 3
+
+
+def test_points_in_their_octants(lod):
+    _, xyz, _, t = lod
+    for i in range(len(t.nodes)):
+        f, c = int(t.nodes[i]["first"]), int(t.nodes[i]["count"])
+        pts = xyz[t.perm[f:f + c]]
+        lo = t.nodes[i]["min"]
+        # every ancestor split puts the point on its node's side of the midpoint
+        node = i
+        while node != 0:
+            par = int(t.parent[node])
+            half = np.float32(t.nodes[par]["size"][0] * np.float32(0.5))
+            mid = (t.nodes[par]["min"] + half).astype(np.float32)
+            for a in range(3):
+                upper = t.nodes[node]["min"][a] != t.nodes[par]["min"][a]
+                assert np.all((pts[:, a] >= mid[a]) == upper)
+            node = par
+        assert np.all(pts >= lo)
+
+
+def test_parent_keeps_lowest_priorities_of_subtree(lod):
+    _, xyz, _, t = lod
+    ch = _children(t)
+
+    def subtree(i):
+        f, c = int(t.nodes[i]["first"]), int(t.nodes[i]["count"])
+        out = list(t.perm[f:f + c])
+        for cc in ch[i]:
+            out += subtree(cc)
+        return out
+
+    pri = lambda idx: (O.splitmix64((SEED << 32) + int(idx)), int(idx))
+    for i in [0] + ch[0][:3]:
+        if not ch[i]:
+            continue
+        allpts = subtree(i)
+        want = sorted(sorted(allpts, key=pri)[:M])
+        f, c = int(t.nodes[i]["first"]), int(t.nodes[i]["count"])
+        assert list(t.perm[f:f + c]) == want          # kept in input order
+
+
+def test_subset_is_spatially_uniform(lod):
+    """The root's subset covers the area like the whole cloud (uniform draw)."""
+    _, xyz, _, t = lod
+    root = xyz[t.perm[:M]]
+    h_all, _ = np.histogram(xyz[:, 0], bins=8, range=(xyz[:, 0].min(), xyz[:, 0].max()))
+    h_root, _ = np.histogram(root[:, 0], bins=8, range=(xyz[:, 0].min(), xyz[:, 0].max()))
+    assert np.abs(h_root / M - h_all / len(xyz)).max() < 0.03
+
+
+def test_words_are_eq1_against_node_cube(lod):
+    _, xyz, _, t = lod
+    for i in range(0, len(t.nodes), 5):
+        b = t.nodes[i]
+        f, c = int(b["first"]), int(b["count"])
+        for j in range(f, f + c, 97):
+            p = xyz[t.perm[j]]
+            q = [O.quantize30(p[a], b["min"][a], b["size"][a]) for a in range(3)]
+            assert O.split_words(*q) == [int(t.w1[j]), int(t.w2[j]), int(t.w3[j])]
+
+
+def test_selection_rules(lod):
+    p, xyz, _, t = lod
+    for vi in range(5):
+        m = S.random_view(p, vi, 160, 120, seed=11)
+        v = O.make_view(m, 160, 120)
+        sel_all = O.lod_select(t, v, 0.0)
+        sel_300 = O.lod_select(t, v, 300.0)
+        sel_big = O.lod_select(t, v, 1e9)
+        for i in range(len(t.nodes)):
+            in_frustum = not O.cull(t.nodes[i], v)
+            par_ok = i == 0 or sel_all[int(t.parent[i])]
+            assert sel_all[i] == (in_frustum and par_ok)
+            if sel_300[i]:
+                assert sel_all[i]
+                if i:
+                    e = O.projected_extent(t.nodes[i], v)
+                    assert e is None or not (e < 300.0)
+                    assert sel_300[int(t.parent[i])]
+        # with a huge threshold only the root and nodes reaching behind the
+        # eye (a corner with w <= 0 counts as large) remain
+        for i in np.nonzero(sel_big)[0][1:]:
+            assert O.projected_extent(t.nodes[i], v) is None
+        assert sel_300.sum() <= sel_all.sum()
+
+
+def test_lod_render_all_nodes_equals_plain_render(lod):
+    """With no size threshold, the LOD pass draws exactly the in-frustum nodes,
+    which (culling being conservative) equals a plain render of all nodes."""
+    p, xyz, _, t = lod
+    m = S.random_view(p, 2, 120, 90, seed=11)
+    v = O.make_view(m, 120, 90)
+    lvis, lst = O.lod_render(t, v, 0.0)
+    enc = O.Encoded(t.nodes, t.w1, t.w2, t.w3, t.color, t.perm)
+    pvis, _ = O.render(enc, v)
+    assert np.array_equal(lvis, pvis)
+    svis, sst = O.lod_render(t, v, 200.0)
+    assert sst["points_processed"] < lst["points_processed"]
