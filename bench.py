@@ -38,6 +38,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gpoints/s & ms/frame at 2B pts 1080p; %HBM peak; batched views/s, p50/p99"
 
+# DRAM bytes (read + write) of one k_raster1 launch in the ncu capture of the
+# 50M-point overview (profiles/raster_kernel_ncu.md); the traffic of the bench's
+# launch is this scaled by the points processed. Re-capture when the kernel changes.
+RASTER_CAPTURE_POINTS = 50_000_000
+RASTER_CAPTURE_DRAM_BYTES = 209_820_672
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -418,8 +424,10 @@ def main():
     raster_ms = timing.ms_raster / max(1, timing.frames)
     peak, peak_kind = peaks()
     achieved = raster_bytes / (raster_ms / 1e3) / 1e9
+    traffic = RASTER_CAPTURE_DRAM_BYTES * points_per_frame / RASTER_CAPTURE_POINTS
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "ncu capture of the 50M-point overview, scaled by points processed",
                 "kernel": "k_raster", "kernel_ms": raster_ms,
                 "algorithmic_bytes": raster_bytes, "peak_source": peak_kind}
     frame_bytes = raster_bytes + 16 * W * H + 4 * W * H
