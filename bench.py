@@ -64,6 +64,7 @@ def parse():
                     help="Poisson arrival rate of requests per second (offered load)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-lod", action="store_true")
+    ap.add_argument("--no-multiview", action="store_true")
     ap.add_argument("--lod-points", type=float, default=1e9)
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
@@ -267,6 +268,43 @@ def serving_bench(args, pcr, ctx, clouds):
             "one_view_per_launch": single,
             "speedup_vs_one_view_per_launch": batched["views_per_s"] / single["views_per_s"],
             "identical_bits": hb == hs, "all_ok": batched["ok"] and single["ok"]}
+
+
+def multiview_bench(args, pcr, torch, ctx, cloud, params):
+    """Sec. 3.7: a stereo pair (2016x2240 per eye) and a bundle of 8 random
+    1080p views of the resident cloud, in one launch vs one launch per view;
+    the images must be identical."""
+    import pcsynth
+
+    def timed(views, vpl, reps=5):
+        pcr.pc_set_views_per_launch(ctx.h, vpl)
+        fbs = ctx.framebuffers(views)
+        ctx.render(cloud, views, fbs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.render(cloud, views, fbs)
+        e1.record()
+        torch.cuda.synchronize()
+        imgs = [b.cpu() for _, b in fbs]
+        return e0.elapsed_time(e1) / reps, imgs
+
+    out = {}
+    stereo = [pcr.make_view(pcsynth.stereo(params, 2016, 2240, e, 6.5), 2016, 2240, pcr.PC_VIEW_CULL)
+              for e in (0, 1)]
+    bundle = [pcr.make_view(pcsynth.random_view(params, 500 + i, 1920, 1080, seed=args.seed),
+                            1920, 1080, pcr.PC_VIEW_CULL) for i in range(8)]
+    for name, views in (("stereo_2x2016x2240", stereo), ("bundle_8x1080p", bundle)):
+        ms_multi, a = timed(views, 32)
+        ms_single, b = timed(views, 1)
+        out[name] = {"ms_per_view_one_launch": ms_multi / len(views),
+                     "ms_per_view_one_view_per_launch": ms_single / len(views),
+                     "speedup": ms_single / ms_multi,
+                     "identical_bits": all(bool((x == y).all()) for x, y in zip(a, b))}
+    pcr.pc_set_views_per_launch(ctx.h, 32)
+    return out
 
 
 def lod_bench(args, pcr, torch, ctx, params):
@@ -481,6 +519,11 @@ def main():
         serving = serving_bench(args, pcr, ctx, clouds)
         log(args, f"serving: {serving}")
 
+    multiview = None
+    if not args.no_multiview:
+        multiview = multiview_bench(args, pcr, torch, ctx, cloud, params)
+        log(args, f"multiview: {multiview}")
+
     lod = None
     if not args.no_lod:
         lod = lod_bench(args, pcr, torch, ctx, params)
@@ -507,7 +550,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "setup_s": {"generate": t_gen, "encode_upload": t_up}},
                 "roofline": roofline, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
-                "serving": serving, "lod": lod, "autotune": tune,
+                "multiview": multiview, "serving": serving, "lod": lod, "autotune": tune,
                 "gpu_launches": int(timing.launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     ctx.close()
