@@ -24,6 +24,7 @@ the CPU) as the reference arm.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -65,6 +66,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-lod", action="store_true")
     ap.add_argument("--no-multiview", action="store_true")
+    ap.add_argument("--no-order", action="store_true")
+    ap.add_argument("--order-points", type=float, default=2e8)
     ap.add_argument("--lod-points", type=float, default=1e9)
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
@@ -307,6 +310,50 @@ def multiview_bench(args, pcr, torch, ctx, cloud, params):
     return out
 
 
+def order_bench(args, pcr, torch, ctx):
+    """Sec. 4.2: a terrestrial-scan-like terrain cloud (rays from a scanner,
+    20,000 points per scan line, 3 km range) in scan order vs Morton order,
+    from an outside and an inside viewpoint: culled batches, precision mix,
+    ms/frame. Same points, same cameras."""
+    import pcsynth
+    n = int(args.order_points)
+    params = pcsynth.terrain_params(8000.0)
+    xyz, rgba = pcsynth.terrain_scan(n, params, (0.0, 0.0), 3000.0, 20000, seed=args.seed)
+    morton = ctx.upload(xyz, rgba)
+    b, w1, w2, w3, col, _ = pcr.pc_encode(xyz, rgba, 10240, 0, pcr.PC_ENCODE_KEEP_ORDER)
+    scan = ctx.upload_encoded(b, w1, w2, w3, col)
+    del xyz, rgba, b, w1, w2, w3, col
+    h = pcsynth.terrain_height(params, 0.0, 0.0)
+    W, H = args.width, args.height
+    cams = {"outside": pcsynth.look_at_perspective((0, -4200, 2600), (0, 0, 0), (0, 0, 1), 60,
+                                                   W / H, 1, 1e5),
+            "inside": pcsynth.look_at_perspective((0, 0, h + 2.0), (400, 150, h), (0, 0, 1), 70,
+                                                  W / H, 0.5, 1e5)}
+    fbs = ctx.framebuffers([pcr.make_view(cams["outside"], W, H)])
+    out = {"points": n, "scan_lines_points": 20000, "range_m": 3000.0}
+    for cname, m in cams.items():
+        view = pcr.make_view(m, W, H, pcr.PC_VIEW_CULL)
+        for oname, cloud in (("scan_order", scan), ("morton_order", morton)):
+            for _ in range(3):
+                ctx.render(cloud, [view], fbs)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                ctx.render(cloud, [view], fbs)
+            e1.record()
+            torch.cuda.synchronize()
+            out[f"{cname}_{oname}"] = {
+                "ms_per_frame": e0.elapsed_time(e1) / 20,
+                "batches_culled_frac": 1.0 - st["batches_rendered"] / max(1, st["batches_total"]),
+                "batches_k": st["batches_k"][1:], "points_processed": st["points_processed"]}
+    pcr.pc_release_cloud(ctx.h, scan)
+    pcr.pc_release_cloud(ctx.h, morton)
+    return out
+
+
 def lod_bench(args, pcr, torch, ctx, params):
     """Sec. 3.5 on the terrain: a layered octree of --lod-points points (max 12
     levels, <= 10,240 points per node) rendered along the 120-frame fly-through
@@ -501,7 +548,7 @@ def main():
             pcr.pc_render_host(ctx.h, cloud, [view], [hv], stream.cuda_stream)
         dt = time.perf_counter() - t0
         e2e = {"value": points_per_frame * k2 * world / dt / 1e9, "unit": "Gpoints/s",
-               "h2d_bytes_per_step": int(np.dtype(np.uint8).itemsize * 80),
+               "h2d_bytes_per_step": ctypes.sizeof(pcr.pc_view),
                "d2h_bytes_per_step": W * H * 4, "steps": k2,
                "ms_per_step": dt / k2 * 1e3, "api": "pc_render_host"}
 
@@ -523,6 +570,11 @@ def main():
     if not args.no_multiview:
         multiview = multiview_bench(args, pcr, torch, ctx, cloud, params)
         log(args, f"multiview: {multiview}")
+
+    order = None
+    if not args.no_order:
+        order = order_bench(args, pcr, torch, ctx)
+        log(args, f"vertex order: {order}")
 
     lod = None
     if not args.no_lod:
@@ -550,7 +602,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "setup_s": {"generate": t_gen, "encode_upload": t_up}},
                 "roofline": roofline, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
-                "multiview": multiview, "serving": serving, "lod": lod, "autotune": tune,
+                "multiview": multiview, "serving": serving, "lod": lod,
+                "vertex_order": order, "autotune": tune,
                 "gpu_launches": int(timing.launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     ctx.close()

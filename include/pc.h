@@ -56,6 +56,10 @@ typedef uint64_t pc_ticket;   /* 0 is never a valid ticket */
 #define PC_CFG_TIMING 1u      /* record per-pass CUDA events in pc_render */
 #define PC_CFG_GRAPHS 2u      /* replay each frame's kernels as a captured CUDA graph
                                  (updated in place when the views change) */
+#define PC_CFG_KEEP_ORDER 4u  /* pc_upload_cloud: batches of consecutive input points,
+                                 no Morton sort (the unsorted baseline of Sec. 4.2) */
+
+#define PC_ENCODE_KEEP_ORDER 1u   /* pc_encode flag: skip the Morton sort */
 
 typedef struct {
     uint32_t batch_size;          /* points per batch, multiple of 4 (default 10240, Sec. 3.1) */
@@ -106,7 +110,8 @@ const char* pc_last_error(pc_ctx* ctx);
 
 /* Host encoder, alone (no GPU needed). Sorts the n points of xyz (host, n*3
  * floats, x y z per point) by 63-bit Morton code over the cloud's box (21 bits
- * per axis, binary64, ties keep input order), cuts them into batches of
+ * per axis, binary64, ties keep input order; skipped with PC_ENCODE_KEEP_ORDER
+ * in flags), cuts them into batches of
  * batch_size consecutive points, computes each batch's binary32 box and writes
  * Eq. 1's 30-bit coordinates split into three words per point. Outputs (host,
  * caller-allocated): batches[ceil(n / batch_size)], w1/w2/w3/color[n] in sorted
@@ -114,11 +119,12 @@ const char* pc_last_error(pc_ctx* ctx);
  * (colour 0). threads = 0 uses all cores. PC_EINVAL if n >= 2^32 or batch_size
  * is 0 or not a multiple of 4. */
 pc_status pc_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
-                    uint32_t batch_size, uint32_t threads, pc_batch* batches,
+                    uint32_t batch_size, uint32_t threads, uint32_t flags, pc_batch* batches,
                     uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color,
                     uint32_t* perm);
 
-/* Encode host points (as pc_encode, batch size from the context's config) and
+/* Encode host points (as pc_encode, batch size and PC_CFG_KEEP_ORDER from the
+ * context's config) and
  * upload the cloud to device memory owned by the library. Synchronous. xyz and
  * rgba are read only during the call. *out receives a cloud handle. */
 pc_status pc_upload_cloud(pc_ctx* ctx, const float* xyz, const uint32_t* rgba,
@@ -187,12 +193,20 @@ pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
 #define PC_VIEW_NO_EARLY_DEPTH 2u          /* skip the non-atomic depth pre-test */
 #define PC_VIEW_FORCE_K(k)     (((uint32_t)(k) & 3u) << 4)  /* 1..3: fixed precision */
 #define PC_VIEW_K_MASK         0x30u
+#define PC_VIEW_DILATE         0x40u       /* depth-aware dilation in the resolve (Sec. 3.7):
+                                              each pixel shows the closest point within 3x3,
+                                              5x5 or 7x7 pixels by its ring (see lod_px_periphery) */
 
 typedef struct {
     float    view_proj[16];   /* world -> clip, column-major */
     uint32_t width, height;   /* 1..16384 */
     uint32_t flags;           /* PC_VIEW_* */
     float    lod_px;          /* LOD clouds: node threshold in px (Sec. 3.5); 0 = all nodes */
+    float    lod_px_periphery;/* > 0: foveated thresholds (Sec. 3.7) by the ring of the node's
+                                 projected centre: lod_px within a third of the half-diagonal
+                                 from the view centre, the mean of both within two thirds,
+                                 lod_px_periphery beyond; 0: lod_px everywhere */
+    uint32_t reserved[3];
 } pc_view;
 
 /* Caller-owned device framebuffer of one view: vis[width*height] (uint64 keys)

@@ -107,6 +107,8 @@ def lib():
             L.or_num_batches.restype = u64
             L.or_encode.argtypes = [vp, vp, u64, u32, vp, vp, vp, vp, vp, vp]
             L.or_encode.restype = i32
+            L.or_encode_in_order.argtypes = [vp, vp, u64, u32, vp, vp, vp, vp, vp]
+            L.or_encode_in_order.restype = i32
             L.or_project_position.argtypes = [vp, VP, u32, vp, vp, vp]
             L.or_project_position.restype = i32
             L.or_project_point.argtypes = [vp, i32, u32, u32, u32, u32, VP, vp, vp]
@@ -130,8 +132,11 @@ def lib():
             L.or_lod_count_nodes.restype = ctypes.c_int64
             L.or_lod_build.argtypes = [vp, vp, u64, u32, u32, u32, vp, vp, vp, vp, vp, vp, vp, vp]
             L.or_lod_build.restype = ctypes.c_int64
-            L.or_lod_select.argtypes = [vp, vp, u64, VP, f32, vp]
-            L.or_lod_render.argtypes = [vp, vp, u64, vp, vp, vp, VP, f32, vp, SP]
+            L.or_lod_select.argtypes = [vp, vp, u64, VP, f32, f32, vp]
+            L.or_lod_render.argtypes = [vp, vp, u64, vp, vp, vp, VP, f32, f32, vp, SP]
+            L.or_ring.argtypes = [f32, f32, u32, u32]
+            L.or_ring.restype = i32
+            L.or_resolve_dilated.argtypes = [vp, u32, u32, vp, vp]
             _lib = L
     return _lib
 
@@ -208,6 +213,21 @@ def encode(xyz: np.ndarray, rgba: np.ndarray, batch_size: int = 10240) -> Encode
     if rc < 0:
         raise RuntimeError(f"or_encode failed: {rc}")
     return Encoded(batches, w1, w2, w3, color, perm)
+
+
+def encode_in_order(xyz: np.ndarray, rgba: np.ndarray, batch_size: int = 10240) -> Encoded:
+    """Batches of consecutive input points, no Morton sort (Sec. 4.2 baseline)."""
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    rgba = np.ascontiguousarray(rgba, np.uint32)
+    n = len(rgba)
+    nb = lib().or_num_batches(n, batch_size)
+    batches = np.zeros(nb, BATCH_DTYPE)
+    w = [np.zeros(n, np.uint32) for _ in range(4)]
+    rc = lib().or_encode_in_order(_p(xyz), _p(rgba), n, batch_size, _p(batches),
+                                  *(_p(a) for a in w))
+    if rc < 0:
+        raise RuntimeError(f"or_encode_in_order failed: {rc}")
+    return Encoded(batches, w[0], w[1], w[2], w[3], np.arange(n, dtype=np.uint32))
 
 
 # ---- Listing 1 and the geometry pass -----------------------------------------
@@ -327,19 +347,32 @@ def lod_build(xyz, rgba, max_levels=12, max_node_points=10240, seed=0) -> LodClo
                     w[3][:n], w[4][:n])
 
 
-def lod_select(lod: LodCloud, view: View, lod_px: float):
+def lod_select(lod: LodCloud, view: View, lod_px: float, lod_px_periphery: float = 0.0):
     sel = np.zeros(max(len(lod.nodes), 1), np.uint8)
     lib().or_lod_select(_p(lod.nodes), _p(lod.parent), len(lod.nodes), ctypes.byref(view),
-                        float(lod_px), _p(sel))
+                        float(lod_px), float(lod_px_periphery), _p(sel))
     return sel[:len(lod.nodes)]
 
 
-def lod_render(lod: LodCloud, view: View, lod_px: float):
+def lod_render(lod: LodCloud, view: View, lod_px: float, lod_px_periphery: float = 0.0):
     vis = np.empty(view.width * view.height, np.uint64)
     st = Stats()
     lib().or_lod_render(_p(lod.nodes), _p(lod.parent), len(lod.nodes), _p(lod.w1), _p(lod.w2),
-                        _p(lod.w3), ctypes.byref(view), float(lod_px), _p(vis), ctypes.byref(st))
+                        _p(lod.w3), ctypes.byref(view), float(lod_px), float(lod_px_periphery),
+                        _p(vis), ctypes.byref(st))
     return vis, st.as_dict()
+
+
+def ring(x: float, y: float, width: int, height: int) -> int:
+    return lib().or_ring(float(np.float32(x)), float(np.float32(y)), width, height)
+
+
+def resolve_dilated(vis: np.ndarray, width: int, height: int, color: np.ndarray):
+    vis = np.ascontiguousarray(vis, np.uint64)
+    color = np.ascontiguousarray(color, np.uint32)
+    out = np.empty(width * height, np.uint32)
+    lib().or_resolve_dilated(_p(vis), width, height, _p(color), _p(out))
+    return out
 
 
 def decode_cloud(enc: Encoded, k: int = 3) -> np.ndarray:

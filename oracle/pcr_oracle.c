@@ -158,6 +158,44 @@ int or_encode(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch
     return (int)(nb > 0x7FFFFFFF ? 0x7FFFFFFF : nb);
 }
 
+int or_encode_in_order(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
+                       or_batch* batches, uint32_t* w1, uint32_t* w2, uint32_t* w3,
+                       uint32_t* color) {
+    if (batch_size == 0 || n > 0xFFFFFFFFull) return -1;
+    uint64_t nb = or_num_batches(n, batch_size);
+    for (uint64_t b = 0; b < nb; ++b) {
+        uint64_t first = b * batch_size;
+        uint64_t end = first + batch_size < n ? first + batch_size : n;
+        float bmin[3], bmax[3];
+        for (int a = 0; a < 3; ++a) bmin[a] = bmax[a] = xyz[3 * first + a];
+        for (uint64_t j = first; j < end; ++j)
+            for (int a = 0; a < 3; ++a) {
+                float v = xyz[3 * j + a];
+                if (v < bmin[a]) bmin[a] = v;
+                if (v > bmax[a]) bmax[a] = v;
+            }
+        or_batch* B = &batches[b];
+        for (int a = 0; a < 3; ++a) {
+            B->min[a] = bmin[a];
+            B->size[a] = bmax[a] - bmin[a];
+        }
+        B->first = (uint32_t)first;
+        B->count = (uint32_t)(end - first);
+        for (uint64_t j = first; j < end; ++j) {
+            const float* p = &xyz[3 * j];
+            uint32_t w[3];
+            or_split_words(or_quantize30(p[0], B->min[0], B->size[0]),
+                           or_quantize30(p[1], B->min[1], B->size[1]),
+                           or_quantize30(p[2], B->min[2], B->size[2]), w);
+            w1[j] = w[0];
+            w2[j] = w[1];
+            w3[j] = w[2];
+            color[j] = rgba[j];
+        }
+    }
+    return (int)(nb > 0x7FFFFFFF ? 0x7FFFFFFF : nb);
+}
+
 /* ---- Sec. 3.3 decode and Listing 1 projection ---------------------------- */
 
 void or_decode_position(const or_batch* b, int k, uint32_t w1, uint32_t w2,
@@ -435,8 +473,20 @@ void or_resolve(const uint64_t* vis, uint64_t npixels, const uint32_t* color,
 
 /* ---- Sec. 3.5 level of detail --------------------------------------------- */
 
+static int projected_box(const or_batch* b, const or_view* v, float fmin[2], float fmax[2]);
+
 int or_projected_extent(const or_batch* b, const or_view* v, float* extent) {
-    float fmin[2] = {0, 0}, fmax[2] = {0, 0};
+    float fmin[2], fmax[2];
+    if (!projected_box(b, v, fmin, fmax)) return 0;
+    float ex = fmax[0] - fmin[0];
+    float ey = fmax[1] - fmin[1];
+    if (ex != ex || ey != ey) *extent = ex + ey;   /* NaN: never below a threshold */
+    else *extent = ex > ey ? ex : ey;
+    return 1;
+}
+
+/* the 8 corners' unfloored pixel coordinates: min and max per axis */
+static int projected_box(const or_batch* b, const or_view* v, float fmin[2], float fmax[2]) {
     for (int c = 0; c < 8; ++c) {
         float p[3];
         for (int a = 0; a < 3; ++a)
@@ -453,11 +503,17 @@ int or_projected_extent(const or_batch* b, const or_view* v, float* extent) {
             if (c == 0 || f[a] > fmax[a]) fmax[a] = f[a];
         }
     }
-    float ex = fmax[0] - fmin[0];
-    float ey = fmax[1] - fmin[1];
-    if (ex != ex || ey != ey) *extent = ex + ey;   /* NaN: never below a threshold */
-    else *extent = ex > ey ? ex : ey;
     return 1;
+}
+
+int or_ring(float x, float y, uint32_t width, uint32_t height) {
+    float hw = (float)width * 0.5f, hh = (float)height * 0.5f;
+    float dx = x - hw, dy = y - hh;
+    float d2 = dx * dx + dy * dy;
+    float r2 = hw * hw + hh * hh;
+    if (9.0f * d2 < r2) return 0;
+    if (9.0f * d2 < 4.0f * r2) return 1;
+    return 2;
 }
 
 uint64_t or_splitmix64(uint64_t z) {
@@ -620,12 +676,24 @@ int64_t or_lod_build(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_
 }
 
 void or_lod_select(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
-                   const or_view* v, float lod_px, uint8_t* sel) {
+                   const or_view* v, float lod_px, float lod_px_periphery, uint8_t* sel) {
     for (uint64_t i = 0; i < nnodes; ++i) {
         int ok = !or_cull(&nodes[i], v);
         if (ok && i > 0) {
             float e;
-            if (or_projected_extent(&nodes[i], v, &e)) ok = !(e < lod_px);
+            if (or_projected_extent(&nodes[i], v, &e)) {
+                float t = lod_px;
+                if (lod_px_periphery > 0.0f) {
+                    float fmin[2], fmax[2];
+                    projected_box(&nodes[i], v, fmin, fmax);
+                    float cx = (fmin[0] + fmax[0]) * 0.5f;
+                    float cy = (fmin[1] + fmax[1]) * 0.5f;
+                    int ring = or_ring(cx, cy, v->width, v->height);
+                    if (ring == 1) t = (lod_px + lod_px_periphery) * 0.5f;
+                    if (ring == 2) t = lod_px_periphery;
+                }
+                ok = !(e < t);
+            }
         }
         if (ok && i > 0) ok = sel[parent[i]];
         sel[i] = (uint8_t)ok;
@@ -634,12 +702,13 @@ void or_lod_select(const or_batch* nodes, const uint32_t* parent, uint64_t nnode
 
 void or_lod_render(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
                    const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
-                   const or_view* v, float lod_px, uint64_t* vis, or_stats* st) {
+                   const or_view* v, float lod_px, float lod_px_periphery, uint64_t* vis,
+                   or_stats* st) {
     uint64_t npix = (uint64_t)v->width * v->height;
     for (uint64_t p = 0; p < npix; ++p) vis[p] = OR_EMPTY;
     if (st) memset(st, 0, sizeof(*st));
     uint8_t* sel = (uint8_t*)malloc(nnodes ? nnodes : 1);
-    or_lod_select(nodes, parent, nnodes, v, lod_px, sel);
+    or_lod_select(nodes, parent, nnodes, v, lod_px, lod_px_periphery, sel);
     for (uint64_t i = 0; i < nnodes; ++i) {
         if (!sel[i]) continue;
         const or_batch* b = &nodes[i];
@@ -660,4 +729,22 @@ void or_lod_render(const or_batch* nodes, const uint32_t* parent, uint64_t nnode
         }
     }
     free(sel);
+}
+
+void or_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height,
+                        const uint32_t* color, uint32_t* out) {
+    for (uint32_t py = 0; py < height; ++py)
+        for (uint32_t px = 0; px < width; ++px) {
+            int r = 1 + or_ring((float)px + 0.5f, (float)py + 0.5f, width, height);
+            uint64_t best = OR_EMPTY;
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    int x = (int)px + dx, y = (int)py + dy;
+                    if (x < 0 || y < 0 || x >= (int)width || y >= (int)height) continue;
+                    uint64_t k = vis[(uint64_t)y * width + (uint64_t)x];
+                    if (k < best) best = k;
+                }
+            out[(uint64_t)py * width + px] =
+                best == OR_EMPTY ? 0u : color[(uint32_t)(best & 0xFFFFFFFFull)];
+        }
 }

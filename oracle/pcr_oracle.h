@@ -73,6 +73,12 @@ int or_encode(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch
               uint32_t* perm, or_batch* batches, uint32_t* w1, uint32_t* w2,
               uint32_t* w3, uint32_t* color);
 
+/* The same without the Morton sort: batches of consecutive input points
+ * (the unsorted baseline of Sec. 4.2). */
+int or_encode_in_order(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
+                       or_batch* batches, uint32_t* w1, uint32_t* w2, uint32_t* w3,
+                       uint32_t* color);
+
 /* Listing 1: project one world position. Returns 1 and writes the pixel id
  * (py * width + px) and the 64-bit key (bits of w_clip << 32 | idx) when the
  * point lands in the viewport, else 0. When fxy is not NULL it receives the
@@ -147,18 +153,35 @@ int64_t or_lod_build(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_
                      uint32_t* parent, uint32_t* level, uint32_t* perm, uint32_t* w1,
                      uint32_t* w2, uint32_t* w3, uint32_t* color);
 
+/* Sec. 3.7 rings of a screen position (x, y) in pixels: 0 within a third of
+ * the half-diagonal from the view centre, 1 within two thirds, else 2;
+ * binary32: d2 = dx*dx + dy*dy, R2 = (W/2)^2 + (H/2)^2, ring 0 iff 9 d2 < R2,
+ * ring 1 iff 9 d2 < 4 R2. */
+int or_ring(float x, float y, uint32_t width, uint32_t height);
+
 /* Sec. 3.5 node selection: node n is drawn when it is in the frustum (the
- * culling test of Sec. 3.2), its projected extent is at least lod_px (any
- * corner with w <= 0 counts as large; the root needs only the frustum test),
- * and its parent is drawn. sel[n] = 1 for drawn nodes. Nodes must be in
- * breadth-first order (parents first). */
+ * culling test of Sec. 3.2), its projected extent is at least its threshold
+ * (any corner with w <= 0 counts as large; the root needs only the frustum
+ * test), and its parent is drawn. The threshold is lod_px, or with
+ * lod_px_periphery > 0 (Sec. 3.7 foveation) lod_px in ring 0,
+ * (lod_px + lod_px_periphery) * 0.5 in ring 1 and lod_px_periphery in ring 2,
+ * the ring of the centre of the node's projected corner box. sel[n] = 1 for
+ * drawn nodes. Nodes must be in breadth-first order (parents first). */
 void or_lod_select(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
-                   const or_view* v, float lod_px, uint8_t* sel);
+                   const or_view* v, float lod_px, float lod_px_periphery, uint8_t* sel);
 
 /* Geometry pass over the drawn nodes of a LOD cloud. */
 void or_lod_render(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
                    const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
-                   const or_view* v, float lod_px, uint64_t* vis, or_stats* st);
+                   const or_view* v, float lod_px, float lod_px_periphery, uint64_t* vis,
+                   or_stats* st);
+
+/* Sec. 3.7 depth-aware dilation: every pixel shows the colour of the smallest
+ * key (the closest point) within a (2r+1) x (2r+1) window, r = 1, 2, 3 in
+ * rings 0, 1, 2 of the pixel centre (px + 0.5, py + 0.5); 0 where the window
+ * is empty. */
+void or_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height,
+                        const uint32_t* color, uint32_t* out);
 
 /* Sec. 3.3 visibility buffer: out[p] = colour of the winning point, 0 where
  * no point landed. */

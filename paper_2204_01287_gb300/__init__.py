@@ -25,8 +25,11 @@ PC_OK, PC_EINVAL, PC_ENOMEM, PC_ENOTFOUND = 0, -1, -2, -3
 PC_EBUSY, PC_ETIMEDOUT, PC_ECUDA, PC_ENOTSUP, PC_EDEVICE = -4, -5, -6, -7, -8
 PC_CFG_TIMING = 1
 PC_CFG_GRAPHS = 2
+PC_CFG_KEEP_ORDER = 4
+PC_ENCODE_KEEP_ORDER = 1
 PC_VIEW_CULL = 1
 PC_VIEW_NO_EARLY_DEPTH = 2
+PC_VIEW_DILATE = 0x40
 EMPTY = 0xFFFFFFFFFFFFFFFF
 
 
@@ -50,7 +53,8 @@ class pc_config(ctypes.Structure):
 class pc_view(ctypes.Structure):
     _fields_ = [("view_proj", ctypes.c_float * 16), ("width", ctypes.c_uint32),
                 ("height", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("lod_px", ctypes.c_float)]
+                ("lod_px", ctypes.c_float), ("lod_px_periphery", ctypes.c_float),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class pc_framebuffer(ctypes.Structure):
@@ -118,7 +122,7 @@ SIGNATURES = [
     ("pc_create", _i32, [_P(_vp), ctypes.c_int, _P(pc_config)]),
     ("pc_destroy", None, [_vp]),
     ("pc_last_error", ctypes.c_char_p, [_vp]),
-    ("pc_encode", _i32, [_vp, _vp, _u64, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("pc_encode", _i32, [_vp, _vp, _u64, _u32, _u32, _u32, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("pc_upload_cloud", _i32, [_vp, _vp, _vp, _u64, _P(_u64)]),
     ("pc_upload_encoded", _i32, [_vp, _vp, _u64, _vp, _vp, _vp, _vp, _u64, _P(_u64)]),
     ("pc_cloud_get_info", _i32, [_vp, _u64, _P(pc_cloud_info)]),
@@ -205,7 +209,7 @@ def _np_ptr(a):
 
 
 def pc_encode(xyz: np.ndarray, rgba: np.ndarray | None, batch_size: int = 10240,
-              threads: int = 0):
+              threads: int = 0, flags: int = 0):
     """Host encoder: returns (batches, w1, w2, w3, color, perm) numpy arrays."""
     xyz = np.ascontiguousarray(xyz, np.float32)
     n = xyz.shape[0]
@@ -214,7 +218,7 @@ def pc_encode(xyz: np.ndarray, rgba: np.ndarray | None, batch_size: int = 10240,
     batches = np.zeros(nb, BATCH_DTYPE)
     w = [np.zeros(n, np.uint32) for _ in range(4)]
     perm = np.zeros(n, np.uint32)
-    rc = lib().pc_encode(_np_ptr(xyz), _np_ptr(rgba), n, batch_size, threads,
+    rc = lib().pc_encode(_np_ptr(xyz), _np_ptr(rgba), n, batch_size, threads, flags,
                          _np_ptr(batches), *(x.ctypes.data for x in w), _np_ptr(perm))
     _check(None, rc)
     return batches, w[0], w[1], w[2], w[3], perm
@@ -284,12 +288,14 @@ def pc_lod_encode(xyz: np.ndarray, rgba, max_levels: int = 12, max_node_points: 
     return nodes[:k], parent[:k], level[:k], w[0][:n], w[1][:n], w[2][:n], w[3][:n], w[4][:n]
 
 
-def make_view(m, width: int, height: int, flags: int = 0, lod_px: float = 0.0) -> pc_view:
+def make_view(m, width: int, height: int, flags: int = 0, lod_px: float = 0.0,
+              lod_px_periphery: float = 0.0) -> pc_view:
     v = pc_view()
     mm = np.asarray(m, np.float32).reshape(16)
     for i in range(16):
         v.view_proj[i] = float(mm[i])
     v.width, v.height, v.flags, v.lod_px = int(width), int(height), int(flags), float(lod_px)
+    v.lod_px_periphery = float(lod_px_periphery)
     return v
 
 

@@ -166,6 +166,7 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
             p.height = pv.height;
             p.flags = pv.flags;
             p.lod_px = pv.lod_px;
+            p.lod_px_periphery = pv.lod_px_periphery;
             p.vis = fbs[base + j].vis;
             p.rgba = fbs[base + j].rgba;
         }
@@ -370,11 +371,12 @@ const char* pc_last_error(pc_ctx* h) {
 }
 
 pc_status pc_encode(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
-                    uint32_t threads, pc_batch* batches, uint32_t* w1, uint32_t* w2,
-                    uint32_t* w3, uint32_t* color, uint32_t* perm) {
+                    uint32_t threads, uint32_t flags, pc_batch* batches, uint32_t* w1,
+                    uint32_t* w2, uint32_t* w3, uint32_t* color, uint32_t* perm) {
     if (n && (!xyz || !batches || !w1 || !w2 || !w3 || !color)) return PC_EINVAL;
     try {
-        return encode_host(xyz, rgba, n, batch_size, threads, batches, w1, w2, w3, color, perm);
+        return encode_host(xyz, rgba, n, batch_size, threads, (flags & PC_ENCODE_KEEP_ORDER) != 0,
+                           batches, w1, w2, w3, color, perm);
     } catch (...) {
         return PC_ENOMEM;
     }
@@ -486,7 +488,8 @@ pc_status pc_upload_cloud(pc_ctx* h, const float* xyz, const uint32_t* rgba, uin
         ctx->fail_msg("host memory for encoding %llu points", (unsigned long long)n);
         return PC_ENOMEM;
     }
-    pc_status rc = pc_encode(xyz, rgba, n, bs, ctx->cfg.encoder_threads, batches.data(),
+    const uint32_t eflags = (ctx->cfg.flags & PC_CFG_KEEP_ORDER) ? PC_ENCODE_KEEP_ORDER : 0u;
+    pc_status rc = pc_encode(xyz, rgba, n, bs, ctx->cfg.encoder_threads, eflags, batches.data(),
                              w1.data(), w2.data(), w3.data(), color.data(), nullptr);
     if (rc != PC_OK) {
         ctx->fail_msg("encoder failed: %s", pc_strerror(rc));

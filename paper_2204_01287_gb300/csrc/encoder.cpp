@@ -154,10 +154,51 @@ void lsd_sort(uint64_t* key, uint32_t* idx, uint64_t m, std::vector<uint64_t>& t
     }
 }
 
+// Batches of batch_size consecutive points of the order idx: binary32 box,
+// Eq. 1 and the word split (Sec. 3.1, Eq. 1, Listing 2).
+void encode_batches(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
+                    unsigned threads, const std::vector<uint32_t>& idx, pc_batch* batches,
+                    uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color) {
+    const uint64_t nbatch = (n + batch_size - 1) / batch_size;
+    parallel_dynamic(threads, nbatch, 16, [&](unsigned, uint64_t blo, uint64_t bhi) {
+        for (uint64_t b = blo; b < bhi; ++b) {
+            uint64_t f = b * batch_size;
+            uint64_t e = std::min<uint64_t>(n, f + batch_size);
+            float mn[3], mx[3];
+            for (int a = 0; a < 3; ++a) mn[a] = mx[a] = xyz[3 * (uint64_t)idx[f] + a];
+            for (uint64_t j = f; j < e; ++j) {
+                const float* p = &xyz[3 * (uint64_t)idx[j]];
+                for (int a = 0; a < 3; ++a) {
+                    if (p[a] < mn[a]) mn[a] = p[a];
+                    if (p[a] > mx[a]) mx[a] = p[a];
+                }
+            }
+            pc_batch& B = batches[b];
+            for (int a = 0; a < 3; ++a) {
+                B.min[a] = mn[a];
+                B.size[a] = mx[a] - mn[a];
+            }
+            B.first = (uint32_t)f;
+            B.count = (uint32_t)(e - f);
+            for (uint64_t j = f; j < e; ++j) {
+                const float* p = &xyz[3 * (uint64_t)idx[j]];
+                uint32_t q0 = fixed30(p[0], B.min[0], B.size[0]);
+                uint32_t q1 = fixed30(p[1], B.min[1], B.size[1]);
+                uint32_t q2 = fixed30(p[2], B.min[2], B.size[2]);
+                w1[j] = (q0 >> 20) | ((q1 >> 20) << 10) | ((q2 >> 20) << 20);
+                w2[j] = ((q0 >> 10) & 1023u) | (((q1 >> 10) & 1023u) << 10) |
+                        (((q2 >> 10) & 1023u) << 20);
+                w3[j] = (q0 & 1023u) | ((q1 & 1023u) << 10) | ((q2 & 1023u) << 20);
+                color[j] = rgba ? rgba[idx[j]] : 0u;
+            }
+        }
+    });
+}
+
 }  // namespace
 
 pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
-                      uint32_t batch_size, unsigned threads, pc_batch* batches,
+                      uint32_t batch_size, unsigned threads, bool keep_order, pc_batch* batches,
                       uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color,
                       uint32_t* perm_out) {
     if (!xyz && n) return PC_EINVAL;
@@ -166,6 +207,18 @@ pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
     if (n == 0) return PC_OK;
     if (threads == 0) threads = hw_threads();
     threads = std::min<unsigned>(threads, 256);
+    std::vector<uint32_t> idx;
+    if (keep_order) {
+        try {
+            idx.resize(n);
+        } catch (...) {
+            return PC_ENOMEM;
+        }
+        for (uint64_t i = 0; i < n; ++i) idx[i] = (uint32_t)i;
+        if (perm_out) std::memcpy(perm_out, idx.data(), n * sizeof(uint32_t));
+        encode_batches(xyz, rgba, n, batch_size, threads, idx, batches, w1, w2, w3, color);
+        return PC_OK;
+    }
 
     // 1. cloud box
     std::vector<float> tlo(threads * 3), thi(threads * 3);
@@ -205,7 +258,6 @@ pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
     // 2.+3. MSD scatter on the top bits (codes computed twice to save memory)
     const uint64_t nb_top = 1ull << kTopBits;
     std::vector<uint64_t> keys;
-    std::vector<uint32_t> idx;
     try {
         keys.resize(n);
         idx.resize(n);
@@ -255,41 +307,7 @@ pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
     keys.shrink_to_fit();
     if (perm_out) std::memcpy(perm_out, idx.data(), n * sizeof(uint32_t));
 
-    // 4. batches, Eq. 1 and the word split
-    const uint64_t nbatch = (n + batch_size - 1) / batch_size;
-    parallel_dynamic(threads, nbatch, 16, [&](unsigned, uint64_t blo, uint64_t bhi) {
-        for (uint64_t b = blo; b < bhi; ++b) {
-            uint64_t f = b * batch_size;
-            uint64_t e = std::min<uint64_t>(n, f + batch_size);
-            float mn[3], mx[3];
-            for (int a = 0; a < 3; ++a) mn[a] = mx[a] = xyz[3 * (uint64_t)idx[f] + a];
-            for (uint64_t j = f; j < e; ++j) {
-                const float* p = &xyz[3 * (uint64_t)idx[j]];
-                for (int a = 0; a < 3; ++a) {
-                    if (p[a] < mn[a]) mn[a] = p[a];
-                    if (p[a] > mx[a]) mx[a] = p[a];
-                }
-            }
-            pc_batch& B = batches[b];
-            for (int a = 0; a < 3; ++a) {
-                B.min[a] = mn[a];
-                B.size[a] = mx[a] - mn[a];
-            }
-            B.first = (uint32_t)f;
-            B.count = (uint32_t)(e - f);
-            for (uint64_t j = f; j < e; ++j) {
-                const float* p = &xyz[3 * (uint64_t)idx[j]];
-                uint32_t q0 = fixed30(p[0], B.min[0], B.size[0]);
-                uint32_t q1 = fixed30(p[1], B.min[1], B.size[1]);
-                uint32_t q2 = fixed30(p[2], B.min[2], B.size[2]);
-                w1[j] = (q0 >> 20) | ((q1 >> 20) << 10) | ((q2 >> 20) << 20);
-                w2[j] = ((q0 >> 10) & 1023u) | (((q1 >> 10) & 1023u) << 10) |
-                        (((q2 >> 10) & 1023u) << 20);
-                w3[j] = (q0 & 1023u) | ((q1 & 1023u) << 10) | ((q2 & 1023u) << 20);
-                color[j] = rgba ? rgba[idx[j]] : 0u;
-            }
-        }
-    });
+    encode_batches(xyz, rgba, n, batch_size, threads, idx, batches, w1, w2, w3, color);
     return PC_OK;
 }
 

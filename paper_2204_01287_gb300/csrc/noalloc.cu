@@ -106,6 +106,7 @@ extern "C" pc_status pc_render_noalloc(const pc_batch* batches, uint64_t nbatche
     vt.v[0].height = view->height;
     vt.v[0].flags = view->flags;
     vt.v[0].lod_px = view->lod_px;
+    vt.v[0].lod_px_periphery = view->lod_px_periphery;
     vt.v[0].vis = vis;
     vt.v[0].rgba = rgba;
 

@@ -51,6 +51,8 @@ struct ViewParams {
     uint32_t width, height;
     uint32_t flags;       // PC_VIEW_*
     float lod_px;
+    float lod_px_periphery;
+    uint32_t pad;
     uint64_t* vis;        // device, width*height
     uint32_t* rgba;       // device, width*height, may be null
 };
@@ -123,7 +125,7 @@ int raster_occupancy(int threads_per_block, bool multiview);
 // ---- host encoder (encoder.cpp) -------------------------------------------
 
 pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
-                      uint32_t batch_size, unsigned threads, pc_batch* batches,
+                      uint32_t batch_size, unsigned threads, bool keep_order, pc_batch* batches,
                       uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color,
                       uint32_t* perm);
 

@@ -77,10 +77,11 @@ __device__ __forceinline__ float to_pixel(float c, float w, float W) {
 
 // Spread of the 8 projected box corners' unfloored pixel coordinates, with
 // the same binary32 operations as a point; false when a corner has w <= 0.
-__device__ bool corner_extent(const pc_batch& b, const ViewParams& v, float& ex, float& ey) {
+__device__ bool corner_box(const pc_batch& b, const ViewParams& v, float& fmin0, float& fmax0,
+                           float& fmin1, float& fmax1) {
     float hi[3];
     for (int a = 0; a < 3; ++a) hi[a] = __fadd_rn(b.min[a], b.size[a]);
-    float fmin0 = 0.f, fmax0 = 0.f, fmin1 = 0.f, fmax1 = 0.f;
+    fmin0 = fmax0 = fmin1 = fmax1 = 0.f;
     const float W = (float)v.width, H = (float)v.height;
 #pragma unroll 1
     for (int c = 0; c < 8; ++c) {
@@ -96,9 +97,28 @@ __device__ bool corner_extent(const pc_batch& b, const ViewParams& v, float& ex,
         if (c == 0 || f1 < fmin1) fmin1 = f1;
         if (c == 0 || f1 > fmax1) fmax1 = f1;
     }
+    return true;
+}
+
+__device__ bool corner_extent(const pc_batch& b, const ViewParams& v, float& ex, float& ey) {
+    float fmin0, fmax0, fmin1, fmax1;
+    if (!corner_box(b, v, fmin0, fmax0, fmin1, fmax1)) return false;
     ex = __fsub_rn(fmax0, fmin0);
     ey = __fsub_rn(fmax1, fmin1);
     return true;
+}
+
+// Sec. 3.7 rings of a screen position: 0 within a third of the half-diagonal
+// from the view centre, 1 within two thirds, else 2 (binary32, fixed order).
+__device__ __forceinline__ int ring_of(float x, float y, uint32_t width, uint32_t height) {
+    const float hw = __fmul_rn((float)width, 0.5f), hh = __fmul_rn((float)height, 0.5f);
+    const float dx = __fsub_rn(x, hw), dy = __fsub_rn(y, hh);
+    const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    const float r2 = __fadd_rn(__fmul_rn(hw, hw), __fmul_rn(hh, hh));
+    const float d9 = __fmul_rn(9.0f, d2);
+    if (d9 < r2) return 0;
+    if (d9 < __fmul_rn(4.0f, r2)) return 1;
+    return 2;
 }
 
 // Sec. 3.3: smallest k whose cells are below the threshold, from the extent
@@ -189,10 +209,19 @@ __global__ void __launch_bounds__(kCullThreads) k_lod_pass(CloudView c, ViewTabl
         const ViewParams& vp = vt.v[v];
         if (cull_batch(bt, vp)) continue;
         if (n > 0) {
-            float ex, ey;
-            if (corner_extent(bt, vp, ex, ey)) {
+            float fmin0, fmax0, fmin1, fmax1;
+            if (corner_box(bt, vp, fmin0, fmax0, fmin1, fmax1)) {
+                const float ex = __fsub_rn(fmax0, fmin0), ey = __fsub_rn(fmax1, fmin1);
                 const float e = (ex != ex || ey != ey) ? __fadd_rn(ex, ey) : fmaxf(ex, ey);
-                if (e < vp.lod_px) continue;
+                float t = vp.lod_px;
+                if (vp.lod_px_periphery > 0.0f) {
+                    const float cx = __fmul_rn(__fadd_rn(fmin0, fmax0), 0.5f);
+                    const float cy = __fmul_rn(__fadd_rn(fmin1, fmax1), 0.5f);
+                    const int r = ring_of(cx, cy, vp.width, vp.height);
+                    if (r == 1) t = __fmul_rn(__fadd_rn(vp.lod_px, vp.lod_px_periphery), 0.5f);
+                    if (r == 2) t = vp.lod_px_periphery;
+                }
+                if (e < t) continue;
             }
         }
         mask |= 1u << v;
@@ -607,9 +636,23 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
     const ViewParams& vp = vt.v[v];
     if (!vp.rgba) return;
     const uint64_t npix = (uint64_t)vp.width * vp.height;
+    const bool dilate = (vp.flags & PC_VIEW_DILATE) != 0;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long key = vp.vis[p];
+        unsigned long long key = vp.vis[p];
+        if (dilate) {
+            // Sec. 3.7: the closest point within (2r+1)^2 pixels, r by ring
+            const int px = (int)(p % vp.width), py = (int)(p / vp.width);
+            const int r = 1 + ring_of(__fadd_rn((float)px, 0.5f), __fadd_rn((float)py, 0.5f),
+                                      vp.width, vp.height);
+            const int x0 = max(px - r, 0), x1 = min(px + r, (int)vp.width - 1);
+            const int y0 = max(py - r, 0), y1 = min(py + r, (int)vp.height - 1);
+            for (int y = y0; y <= y1; ++y)
+                for (int x = x0; x <= x1; ++x) {
+                    const unsigned long long k = vp.vis[(uint64_t)y * vp.width + x];
+                    if (k < key) key = k;
+                }
+        }
         uint32_t out = 0u;
         if (key != ~0ull) {
             const uint32_t idx = (uint32_t)key;

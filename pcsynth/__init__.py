@@ -78,6 +78,7 @@ def lib():
             L.pcs_terrain_defaults.argtypes = [P, d]
             L.pcs_unit_cube.argtypes = [u64, u64, u64, vp, vp, i32]
             L.pcs_terrain.argtypes = [u64, P, u64, u64, vp, vp, i32]
+            L.pcs_terrain_scan.argtypes = [u64, P, d, d, d, u64, u64, u64, u64, vp, vp, i32]
             L.pcs_terrain_height.argtypes = [u64, P, d, d]
             L.pcs_terrain_height.restype = d
             L.pcs_look_at_perspective.argtypes = [vp, vp, vp, d, d, d, d, vp]
@@ -130,6 +131,22 @@ def terrain(n: int, params: TerrainParams, seed: int = 0, first: int = 0,
         xyz, rgba = out
     lib().pcs_terrain(seed, ctypes.byref(params), first, n, _ptr(xyz), _ptr(rgba),
                       _threads(threads))
+    return xyz, rgba
+
+
+def terrain_scan(n: int, params: TerrainParams, scanner=(0.0, 0.0), max_dist_m: float = 2000.0,
+                 points_per_line: int = 20000, seed: int = 0, first: int = 0, total: int = 0,
+                 threads: int = 0, out=None):
+    """Scan-ordered terrain points (consecutive points along rays from the
+    scanner): (xyz float32[n,3], rgba uint32[n])."""
+    if out is None:
+        xyz = np.empty((n, 3), np.float32)
+        rgba = np.empty(n, np.uint32)
+    else:
+        xyz, rgba = out
+    lib().pcs_terrain_scan(seed, ctypes.byref(params), float(scanner[0]), float(scanner[1]),
+                           float(max_dist_m), total or n, points_per_line, first, n, _ptr(xyz),
+                           _ptr(rgba), _threads(threads))
     return xyz, rgba
 
 

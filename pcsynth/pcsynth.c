@@ -229,6 +229,43 @@ void pcs_terrain(uint64_t seed, const pcs_terrain_params* p, uint64_t first,
     free(c.bld);
 }
 
+/* ---- scan-ordered terrain --------------------------------------------------- */
+
+typedef struct {
+    uint64_t seed, first, total, per_line;
+    const pcs_terrain_params* p;
+    double sx, sy, dmax;
+    float* xyz;
+    uint32_t* rgba;
+} scan_ctx;
+
+static void scan_range(void* c, uint64_t lo, uint64_t hi) {
+    scan_ctx* k = (scan_ctx*)c;
+    const uint64_t lines = (k->total + k->per_line - 1) / k->per_line;
+    for (uint64_t j = lo; j < hi; ++j) {
+        uint64_t i = k->first + j;
+        uint64_t line = i / k->per_line, r = i % k->per_line;
+        double yaw = 2.0 * M_PI * ((double)line + 0.5 * u01(rnd(k->seed, S_X, i))) / (double)lines;
+        double t = ((double)r + u01(rnd(k->seed, S_Y, i))) / (double)k->per_line;
+        double d = 5.0 + (k->dmax - 5.0) * t;
+        double x = k->sx + d * cos(yaw), y = k->sy + d * sin(yaw);
+        double h = pcs_terrain_height(k->seed, k->p, x, y);
+        double z = h + (u01(rnd(k->seed, S_JIT, i)) * 2.0 - 1.0) * k->p->jitter_m;
+        k->xyz[3 * j + 0] = (float)x;
+        k->xyz[3 * j + 1] = (float)y;
+        k->xyz[3 * j + 2] = (float)z;
+        k->rgba[j] = terrain_color(k->seed, k->p, h, i);
+    }
+}
+
+void pcs_terrain_scan(uint64_t seed, const pcs_terrain_params* p, double sx, double sy,
+                      double max_dist_m, uint64_t total, uint64_t points_per_line,
+                      uint64_t first, uint64_t n, float* xyz, uint32_t* rgba, int threads) {
+    if (points_per_line == 0) points_per_line = 1;
+    scan_ctx c = {seed, first, total, points_per_line, p, sx, sy, max_dist_m, xyz, rgba};
+    parallel_range(scan_range, &c, n, threads);
+}
+
 /* ---- cameras -------------------------------------------------------------- */
 
 static void normalize3(double v[3]) {

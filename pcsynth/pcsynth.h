@@ -48,6 +48,15 @@ void pcs_unit_cube(uint64_t seed, uint64_t first, uint64_t n,
 void pcs_terrain(uint64_t seed, const pcs_terrain_params* p, uint64_t first,
                  uint64_t n, float* xyz, uint32_t* rgba, int threads);
 
+/* Points [first, first+n) of a terrestrial-scan-like terrain cloud in scan
+ * order: scan line c = i / points_per_line is a ray from the scanner position
+ * (sx, sy) at yaw 2*pi*c/lines (lines = ceil(total / points_per_line)), and
+ * its points run outward from 5 m to max_dist_m along it, on the terrain
+ * surface; consecutive points therefore form long curves (Sec. 4.2). */
+void pcs_terrain_scan(uint64_t seed, const pcs_terrain_params* p, double sx, double sy,
+                      double max_dist_m, uint64_t total, uint64_t points_per_line,
+                      uint64_t first, uint64_t n, float* xyz, uint32_t* rgba, int threads);
+
 /* Terrain surface height at (x, y), in metres. */
 double pcs_terrain_height(uint64_t seed, const pcs_terrain_params* p,
                           double x, double y);

@@ -59,4 +59,4 @@ def test_host_calls_without_gpu(so):
     h = ctypes.c_void_p()
     assert L.pc_create(None, 0, None) == pcr.PC_EINVAL
     assert L.pc_render(None, 1, None, 0, None, None) == pcr.PC_EINVAL
-    assert L.pc_encode(None, None, 5, 10240, 1, None, None, None, None, None, None) == pcr.PC_EINVAL
+    assert L.pc_encode(None, None, 5, 10240, 1, 0, None, None, None, None, None, None) == pcr.PC_EINVAL

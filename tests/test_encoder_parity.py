@@ -53,3 +53,15 @@ def test_empty_and_invalid():
     assert len(b) == 0
     with pytest.raises(pcr.PCError):
         pcr.pc_encode(np.zeros((4, 3), np.float32), None, batch_size=10)   # not a multiple of 4
+
+
+@pytest.mark.parametrize("n", [7, 30000, 104000])
+def test_keep_order_matches_oracle(n):
+    """Batches of consecutive input points, no Morton sort (Sec. 4.2 baseline)."""
+    xyz, rgba = S.terrain_scan(n, S.terrain_params(4000.0), (0.0, 0.0), 1500.0, 5000, seed=n)
+    enc = O.encode_in_order(xyz, rgba, 10240)
+    b, w1, w2, w3, col, perm = pcr.pc_encode(xyz, rgba, 10240, 0, pcr.PC_ENCODE_KEEP_ORDER)
+    assert np.array_equal(perm, np.arange(n))
+    assert b.tobytes() == enc.batches.tobytes()
+    for a, r in ((w1, enc.w1), (w2, enc.w2), (w3, enc.w3), (col, enc.color)):
+        assert np.array_equal(a, r)

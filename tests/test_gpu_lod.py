@@ -78,3 +78,38 @@ def test_lod_threshold_reduces_work(lodworld):
         processed.append(ctx.stats()["points_processed"])
     assert all(a >= b for a, b in zip(processed, processed[1:])) and processed[-1] > 0
     assert processed[0] > processed[-1]
+
+
+@pytest.mark.parametrize("frame", [10, 64])
+def test_foveated_lod_and_dilation_match_oracle(lodworld, frame):
+    """Sec. 3.7: thresholds of 100 px in the centre, 200 px between and 300 px in
+    the periphery, and the depth-aware 3x3 .. 7x7 dilation in the resolve."""
+    import torch
+    ctx, p, lod, ref = lodworld
+    W, H = 300, 200
+    m = S.flythrough(p, frame, 120, W, H, seed=12)
+    v = pcr.make_view(m, W, H, pcr.PC_VIEW_CULL | pcr.PC_VIEW_DILATE, 100.0, 300.0)
+    [(vis, img)] = ctx.render(lod, [v])
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ovis, ost = O.lod_render(ref, O.make_view(m, W, H), 100.0, 300.0)
+    assert np.array_equal(pcr.vis_to_numpy(vis), ovis)
+    assert np.array_equal(pcr.rgba_to_numpy(img), O.resolve_dilated(ovis, W, H, ref.color))
+    assert st["batches_rendered"] == ost["batches_rendered"]
+    _, flat = O.lod_render(ref, O.make_view(m, W, H), 100.0)
+    assert ost["points_processed"] <= flat["points_processed"]
+
+
+def test_dilation_on_plain_cloud(cuda_lib):
+    import torch
+    p = S.terrain_params(3000.0)
+    xyz, rgba = S.terrain(200_000, p, seed=13)
+    enc = O.encode(xyz, rgba, 10240)
+    with pcr.Context(0) as ctx:
+        cloud = ctx.upload(xyz, rgba)
+        m = S.random_view(p, 4, 180, 120, seed=13)
+        [(vis, img)] = ctx.render(cloud, [pcr.make_view(m, 180, 120, pcr.PC_VIEW_DILATE)])
+        torch.cuda.synchronize()
+        ovis, _ = O.render(enc, O.make_view(m, 180, 120))
+        assert np.array_equal(pcr.vis_to_numpy(vis), ovis)
+        assert np.array_equal(pcr.rgba_to_numpy(img), O.resolve_dilated(ovis, 180, 120, enc.color))

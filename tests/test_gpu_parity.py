@@ -313,3 +313,24 @@ def test_large_view(ctx, terrain_small):
     [(vis, img)] = gpu_render(ctx, cloud, [pcr.make_view(m, W, H, pcr.PC_VIEW_CULL)])
     ovis, _ = O.render(enc, oracle_view(m, W, H))
     assert_same(vis, img, ovis, enc.color, "wide view")
+
+
+def test_scan_order_cloud_keep_order(cuda_lib):
+    """Sec. 4.2 baseline: batches of consecutive scan-order points, no Morton
+    sort; adaptive precision and culling still match the oracle bit for bit."""
+    import torch
+    p = S.terrain_params(6000.0)
+    xyz, rgba = S.terrain_scan(400_000, p, (0.0, 0.0), 2000.0, 8000, seed=4)
+    enc = O.encode_in_order(xyz, rgba, 10240)
+    c = pcr.Context(0, flags=pcr.PC_CFG_KEEP_ORDER)
+    try:
+        cloud = c.upload(xyz, rgba)
+        h = S.terrain_height(p, 0.0, 0.0)
+        views = [S.look_at_perspective((0, -2500, 1800), (0, 0, 0), (0, 0, 1), 60, 16 / 9, 1, 1e5),
+                 S.look_at_perspective((0, 0, h + 2.0), (300, 80, h), (0, 0, 1), 70, 16 / 9, 0.5, 1e5)]
+        for m in views:
+            [(vis, img)] = gpu_render(c, cloud, [pcr.make_view(m, 256, 144, pcr.PC_VIEW_CULL)])
+            ovis, _ = O.render(enc, oracle_view(m, 256, 144))
+            assert_same(vis, img, ovis, enc.color, "scan order")
+    finally:
+        c.close()

@@ -160,3 +160,50 @@ def test_lod_render_all_nodes_equals_plain_render(lod):
     assert np.array_equal(lvis, pvis)
     svis, sst = O.lod_render(t, v, 200.0)
     assert sst["points_processed"] < lst["points_processed"]
+
+
+# ---- Sec. 3.7 foveated thresholds and depth-aware dilation --------------------------
+
+@pytest.mark.parametrize("x,y,want", [(45, 45, 0), (66, 45, 0), (67, 45, 1), (87, 45, 1),
+                                      (88, 45, 2), (45, 24, 0), (0, 0, 2), (45, 3, 1)])
+def test_ring_boundaries(x, y, want):
+    """90x90 view: R2 = 45^2 + 45^2 = 4050; ring 0 iff 9 d2 < 4050 (d2 < 450,
+    d <= 21), ring 1 iff 9 d2 < 16200 (d2 < 1800, d <= 42); hand-computed."""
+    assert O.ring(x, y, 90, 90) == want
+
+
+def test_dilation_window_grows_with_ring():
+    W = H = 90
+    color = np.array([0xAA, 0xBB], np.uint32)
+    vis = np.full(W * H, O.EMPTY, np.uint64)
+    vis[45 * W + 45] = (5 << 32) | 0          # centre point: 3x3
+    vis[2 * W + 2] = (5 << 32) | 1            # corner point: 7x7 (ring 2 pixels)
+    out = O.resolve_dilated(vis, W, H, color).reshape(H, W)
+    assert (out[44:47, 44:47] == 0xAA).all() and out[43, 45] == 0 and out[45, 47] == 0
+    assert (out[0:6, 0:6] == 0xBB).all() and out[6, 2] == 0
+    assert (out == 0xAA).sum() == 9
+
+
+def test_dilation_is_depth_aware():
+    W, H = 90, 90
+    color = np.array([1, 2], np.uint32)
+    vis = np.full(W * H, O.EMPTY, np.uint64)
+    vis[45 * W + 45] = (9 << 32) | 0          # farther
+    vis[45 * W + 46] = (3 << 32) | 1          # nearer: wins wherever both are in reach
+    out = O.resolve_dilated(vis, W, H, color).reshape(H, W)
+    assert out[45, 45] == 2 and out[45, 44] == 1 and out[44, 46] == 2
+
+
+def test_foveated_selection(lod):
+    p, xyz, _, t = lod
+    for vi in range(4):
+        v = O.make_view(S.random_view(p, 10 + vi, 160, 120, seed=11), 160, 120)
+        flat = O.lod_select(t, v, 100.0)
+        fov = O.lod_select(t, v, 100.0, 300.0)
+        same = O.lod_select(t, v, 100.0, 100.0)
+        assert np.array_equal(flat, same)
+        assert np.all(fov <= flat) and fov.sum() >= 1
+        for i in np.nonzero(fov)[0][1:]:
+            e = O.projected_extent(t.nodes[i], v)
+            if e is not None:
+                assert e >= 100.0
