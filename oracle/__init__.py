@@ -137,6 +137,9 @@ def lib():
             L.or_ring.argtypes = [f32, f32, u32, u32]
             L.or_ring.restype = i32
             L.or_resolve_dilated.argtypes = [vp, u32, u32, vp, vp]
+            L.or_render_hqs.argtypes = [vp, u64, vp, vp, vp, vp, VP, vp, vp]
+            L.or_lod_render_hqs.argtypes = [vp, vp, u64, vp, vp, vp, vp, VP, f32, f32, vp, vp]
+            L.or_hqs_resolve_dilated.argtypes = [vp, u32, u32, vp, vp]
             _lib = L
     return _lib
 
@@ -381,3 +384,32 @@ def decode_cloud(enc: Encoded, k: int = 3) -> np.ndarray:
     lib().or_decode_cloud(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2),
                           _p(enc.w3), int(k), _p(out))
     return out[:enc.n]
+
+
+def render_hqs(enc: Encoded, view: View, vis: np.ndarray):
+    """Sec. 3.6 high-quality shading image after the geometry pass `vis`."""
+    vis = np.ascontiguousarray(vis, np.uint64)
+    out = np.empty(view.width * view.height, np.uint32)
+    lib().or_render_hqs(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2), _p(enc.w3),
+                        _p(enc.color), ctypes.byref(view), _p(vis), _p(out))
+    return out
+
+
+def lod_render_hqs(lod: LodCloud, view: View, vis: np.ndarray, lod_px: float,
+                   lod_px_periphery: float = 0.0):
+    """Sec. 3.6 high-quality shading image of a LOD cloud after its geometry pass."""
+    vis = np.ascontiguousarray(vis, np.uint64)
+    out = np.empty(view.width * view.height, np.uint32)
+    lib().or_lod_render_hqs(_p(lod.nodes), _p(lod.parent), len(lod.nodes), _p(lod.w1),
+                            _p(lod.w2), _p(lod.w3), _p(lod.color), ctypes.byref(view),
+                            float(lod_px), float(lod_px_periphery), _p(vis), _p(out))
+    return out
+
+
+def hqs_resolve_dilated(vis: np.ndarray, width: int, height: int, hqs: np.ndarray):
+    """Depth-aware dilation (Sec. 3.7) of a high-quality shading image."""
+    vis = np.ascontiguousarray(vis, np.uint64)
+    hqs = np.ascontiguousarray(hqs, np.uint32)
+    out = np.empty(width * height, np.uint32)
+    lib().or_hqs_resolve_dilated(_p(vis), width, height, _p(hqs), _p(out))
+    return out

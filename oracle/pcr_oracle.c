@@ -748,3 +748,90 @@ void or_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height,
                 best == OR_EMPTY ? 0u : color[(uint32_t)(best & 0xFFFFFFFFull)];
         }
 }
+
+/* Sec. 3.6, colour pass for one point: it contributes to its pixel when its
+ * depth is within 1% of the closest depth there, w <= fl(w_min * 1.01). */
+static void hqs_point(const or_batch* b, int k, uint32_t idx, const uint32_t* w1,
+                      const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
+                      const or_view* v, const uint64_t* vis, uint64_t* sum) {
+    uint32_t pix;
+    uint64_t key;
+    if (!or_project_point(b, k, w1[idx], w2[idx], w3[idx], idx, v, &pix, &key)) return;
+    uint32_t wbits = (uint32_t)(vis[pix] >> 32), kbits = (uint32_t)(key >> 32);
+    float wmin, w;
+    memcpy(&wmin, &wbits, 4);
+    memcpy(&w, &kbits, 4);
+    float limit = wmin * 1.01f;
+    if (!(w <= limit)) return;
+    uint32_t c = color[idx];
+    sum[4 * (uint64_t)pix + 0] += c & 255u;
+    sum[4 * (uint64_t)pix + 1] += (c >> 8) & 255u;
+    sum[4 * (uint64_t)pix + 2] += (c >> 16) & 255u;
+    sum[4 * (uint64_t)pix + 3] += 1;
+}
+
+/* Sec. 3.6 resolve: the average of the sums, each channel rounded down. */
+static void hqs_average(const uint64_t* sum, uint64_t npix, uint32_t* out) {
+    for (uint64_t p = 0; p < npix; ++p) {
+        uint64_t n = sum[4 * p + 3];
+        out[p] = n == 0 ? 0u
+                        : (uint32_t)(sum[4 * p + 0] / n) | ((uint32_t)(sum[4 * p + 1] / n) << 8) |
+                              ((uint32_t)(sum[4 * p + 2] / n) << 16) | (255u << 24);
+    }
+}
+
+void or_render_hqs(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                   const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
+                   const or_view* v, const uint64_t* vis, uint32_t* out) {
+    uint64_t npix = (uint64_t)v->width * v->height;
+    uint64_t* sum = (uint64_t*)calloc(npix ? 4 * npix : 1, sizeof(uint64_t));
+    for (uint64_t b = 0; b < nbatches; ++b) {
+        const or_batch* B = &batches[b];
+        if (v->cull && or_cull(B, v)) continue;
+        int k = or_select_k(B, v);
+        for (uint32_t j = 0; j < B->count; ++j)
+            hqs_point(B, k, B->first + j, w1, w2, w3, color, v, vis, sum);
+    }
+    hqs_average(sum, npix, out);
+    free(sum);
+}
+
+void or_lod_render_hqs(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
+                       const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                       const uint32_t* color, const or_view* v, float lod_px,
+                       float lod_px_periphery, const uint64_t* vis, uint32_t* out) {
+    uint64_t npix = (uint64_t)v->width * v->height;
+    uint64_t* sum = (uint64_t*)calloc(npix ? 4 * npix : 1, sizeof(uint64_t));
+    uint8_t* sel = (uint8_t*)malloc(nnodes ? nnodes : 1);
+    or_lod_select(nodes, parent, nnodes, v, lod_px, lod_px_periphery, sel);
+    for (uint64_t i = 0; i < nnodes; ++i) {
+        if (!sel[i]) continue;
+        const or_batch* B = &nodes[i];
+        int k = or_select_k(B, v);
+        for (uint32_t j = 0; j < B->count; ++j)
+            hqs_point(B, k, B->first + j, w1, w2, w3, color, v, vis, sum);
+    }
+    hqs_average(sum, npix, out);
+    free(sel);
+    free(sum);
+}
+
+void or_hqs_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height,
+                            const uint32_t* hqs, uint32_t* out) {
+    for (uint32_t py = 0; py < height; ++py)
+        for (uint32_t px = 0; px < width; ++px) {
+            int r = 1 + or_ring((float)px + 0.5f, (float)py + 0.5f, width, height);
+            uint64_t best = OR_EMPTY, at = 0;
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    int x = (int)px + dx, y = (int)py + dy;
+                    if (x < 0 || y < 0 || x >= (int)width || y >= (int)height) continue;
+                    uint64_t q = (uint64_t)y * width + (uint64_t)x;
+                    if (vis[q] < best) {
+                        best = vis[q];
+                        at = q;
+                    }
+                }
+            out[(uint64_t)py * width + px] = best == OR_EMPTY ? 0u : hqs[at];
+        }
+}

@@ -183,6 +183,28 @@ void or_lod_render(const or_batch* nodes, const uint32_t* parent, uint64_t nnode
 void or_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height,
                         const uint32_t* color, uint32_t* out);
 
+/* Sec. 3.6 high-quality shading: after the geometry pass (vis), every point
+ * that lands on pixel p (same batches, culling, precision and projection as
+ * or_render) with w <= fl(w_min * 1.01), w_min the depth of vis[p], adds its
+ * R, G, B to the pixel's sums and 1 to its count; out[p] = (floor(sumR/n),
+ * floor(sumG/n), floor(sumB/n), 255), 0 where no point landed. */
+void or_render_hqs(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                   const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
+                   const or_view* v, const uint64_t* vis, uint32_t* out);
+
+/* or_render_hqs for a LOD cloud: the points of the nodes that or_lod_select
+ * keeps, each node at its own precision. */
+void or_lod_render_hqs(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
+                       const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
+                       const uint32_t* color, const or_view* v, float lod_px,
+                       float lod_px_periphery, const uint64_t* vis, uint32_t* out);
+
+/* Depth-aware dilation (Sec. 3.7) of a high-quality shading image: out[p] is
+ * hqs[q] of the pixel q holding the smallest key within the window of
+ * or_resolve_dilated around p, 0 where the window is empty. */
+void or_hqs_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height,
+                            const uint32_t* hqs, uint32_t* out);
+
 /* Sec. 3.3 visibility buffer: out[p] = colour of the winning point, 0 where
  * no point landed. */
 void or_resolve(const uint64_t* vis, uint64_t npixels, const uint32_t* color,

@@ -49,9 +49,27 @@ MUTANTS = [
      "uint32_t i = j;\n            uint32_t pix;"),
 ]
 
+# Sec. 3.6 high-quality shading, checked by the pins of tests/test_oracle_hqs.py
+HQS_MUTANTS = [
+    ("hqs_window_open", "if (!(w <= limit)) return;", "if (!(w < limit)) return;"),
+    ("hqs_window_2pct", "float limit = wmin * 1.01f;", "float limit = wmin * 1.02f;"),
+    ("hqs_window_none", "float limit = wmin * 1.01f;", "float limit = wmin;"),
+    ("hqs_channel_shift", "sum[4 * (uint64_t)pix + 1] += (c >> 8) & 255u;",
+     "sum[4 * (uint64_t)pix + 1] += (c >> 16) & 255u;"),
+    ("hqs_no_count", "sum[4 * (uint64_t)pix + 3] += 1;", "sum[4 * (uint64_t)pix + 3] = 1;"),
+    ("hqs_round_up", "(uint32_t)(sum[4 * p + 0] / n)", "(uint32_t)((sum[4 * p + 0] + n - 1) / n)"),
+    ("hqs_lod_unselected", "if (!sel[i]) continue;\n        const or_batch* B = &nodes[i];\n        int k = or_select_k(B, v);\n        for",
+     "const or_batch* B = &nodes[i];\n        int k = or_select_k(B, v);\n        for"),
+    ("hqs_dilate_own_pixel", "best == OR_EMPTY ? 0u : hqs[at];",
+     "best == OR_EMPTY ? 0u : hqs[(uint64_t)py * width + px];"),
+]
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_mutant(tmp_path, name, old, new):
+CASES = ([m + ("test_oracle_pins.py",) for m in MUTANTS] +
+         [m + ("test_oracle_hqs.py",) for m in HQS_MUTANTS])
+
+
+@pytest.mark.parametrize("name,old,new,pins", CASES, ids=[m[0] for m in CASES])
+def test_pins_catch_mutant(tmp_path, name, old, new, pins):
     with open(SRC) as f:
         src = f.read()
     assert old in src, f"mutation site for {name} not found"
@@ -65,6 +83,6 @@ def test_pins_catch_mutant(tmp_path, name, old, new):
                            "-ffp-contract=off", "-o", str(so), str(cfile), "-lm"])
     env = dict(os.environ, PCR_ORACLE_SO=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake {name} was not caught:\n{r.stdout[-2000:]}"
