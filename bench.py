@@ -596,7 +596,6 @@ def main():
                            "points_processed_per_frame": points_per_frame,
                            "batches_rendered": st["batches_rendered"],
                            "batches_k": st["batches_k"][1:],
-                           "points_accepted_per_frame": st["points_accepted"],
                            "points_atomic_per_frame": st["points_atomic"],
                            "l2": "inputs larger than L2 (32 GB cloud vs 129 MB L2)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

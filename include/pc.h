@@ -196,6 +196,18 @@ pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
 #define PC_VIEW_DILATE         0x40u       /* depth-aware dilation in the resolve (Sec. 3.7):
                                               each pixel shows the closest point within 3x3,
                                               5x5 or 7x7 pixels by its ring (see lod_px_periphery) */
+#define PC_VIEW_HQS            0x80u       /* high-quality shading (Sec. 3.6): after the depth pass
+                                              a colour pass sums R, G, B and a count per pixel over
+                                              the points with w <= fl(w_min * 1.01f), two 64-bit
+                                              atomicAdds per point (32-bit sums, exact up to
+                                              16,843,009 points per pixel), and the resolve
+                                              writes the per-channel average (rounded down) with
+                                              alpha 255 */
+#define PC_VIEW_HQS_PACKED     0x100u      /* the same with one 64-bit atomicAdd per point (16-bit
+                                              sums, exact up to 257 points per pixel within the
+                                              window, the case of LOD clouds); a pixel that gets
+                                              more raises the device error flag (PC_EDEVICE). Set
+                                              alone or with PC_VIEW_HQS; takes precedence */
 
 typedef struct {
     float    view_proj[16];   /* world -> clip, column-major */
@@ -211,7 +223,10 @@ typedef struct {
 
 /* Caller-owned device framebuffer of one view: vis[width*height] (uint64 keys)
  * and rgba[width*height] (R | G<<8 | B<<16 | A<<24, 0 where no point landed).
- * rgba may be NULL to skip the resolve. Both 16-byte aligned. */
+ * rgba may be NULL to skip the resolve. Both 16-byte aligned. Views with
+ * PC_VIEW_HQS or PC_VIEW_HQS_PACKED also use a per-pixel sum buffer (16 or
+ * 8 bytes per pixel) that the library owns, one per stream, sized to the
+ * largest launch group of views seen. */
 typedef struct {
     uint64_t* vis;
     uint32_t* rgba;
@@ -242,7 +257,8 @@ pc_status pc_render(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t 
  * static device array of about 3 MB that every GPU loading the library holds
  * until the process exits, so a cloud may have at most
  * 131,072 - n_points / 2^20 - 1 batches; larger ones get PC_EINVAL, as do
- * misaligned or missing buffers. The first call on a device looks up that
+ * misaligned or missing buffers; views with high-quality shading get
+ * PC_ENOTSUP (their sum buffer would need memory). The first call on a device looks up that
  * array's device address (a runtime call, no allocation); make that first
  * call before any stream capture. All calls share the array and reset its
  * counters, so calls that overlap on the GPU (different streams, or different
@@ -267,8 +283,8 @@ typedef struct {
     uint64_t points_k[4];          /* their points */
     uint64_t points_processed;     /* sum of points_k */
     uint64_t words_loaded_bytes;   /* coordinate bytes the raster launch loaded for this view */
-    uint64_t points_accepted;      /* points that landed inside the viewport */
     uint64_t points_atomic;        /* points that issued atomicMin (Table 2 "rendered points") */
+    uint64_t points_blended;       /* high-quality shading: points summed into a pixel */
 } pc_view_stats;
 
 pc_status pc_get_view_stats(pc_ctx* ctx, void* stream, uint32_t view, pc_view_stats* out);
@@ -306,7 +322,8 @@ pc_status pc_set_views_per_launch(pc_ctx* ctx, uint32_t views_per_launch);
 typedef struct {
     uint32_t frames;            /* pc_render calls recorded */
     uint32_t launches;          /* kernels launched by those calls */
-    double   ms_clear, ms_cull, ms_raster, ms_resolve;  /* summed over frames */
+    double   ms_clear, ms_cull, ms_raster, ms_shade, ms_resolve;  /* summed over frames;
+                                   ms_shade: the colour pass of high-quality shading */
     uint64_t raster_launches;
 } pc_timing;
 

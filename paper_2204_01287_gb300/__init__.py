@@ -30,6 +30,8 @@ PC_ENCODE_KEEP_ORDER = 1
 PC_VIEW_CULL = 1
 PC_VIEW_NO_EARLY_DEPTH = 2
 PC_VIEW_DILATE = 0x40
+PC_VIEW_HQS = 0x80
+PC_VIEW_HQS_PACKED = 0x100
 EMPTY = 0xFFFFFFFFFFFFFFFF
 
 
@@ -72,20 +74,23 @@ class pc_view_stats(ctypes.Structure):
                 ("batches_k", ctypes.c_uint64 * 4), ("points_k", ctypes.c_uint64 * 4),
                 ("points_processed", ctypes.c_uint64),
                 ("words_loaded_bytes", ctypes.c_uint64),
-                ("points_accepted", ctypes.c_uint64), ("points_atomic", ctypes.c_uint64)]
+                ("points_atomic", ctypes.c_uint64),
+                ("points_blended", ctypes.c_uint64)]
 
     def as_dict(self):
         return {"batches_total": self.batches_total, "batches_rendered": self.batches_rendered,
                 "batches_k": list(self.batches_k), "points_k": list(self.points_k),
                 "points_processed": self.points_processed,
                 "words_loaded_bytes": self.words_loaded_bytes,
-                "points_accepted": self.points_accepted, "points_atomic": self.points_atomic}
+                "points_atomic": self.points_atomic,
+                "points_blended": self.points_blended}
 
 
 class pc_timing(ctypes.Structure):
     _fields_ = [("frames", ctypes.c_uint32), ("launches", ctypes.c_uint32),
                 ("ms_clear", ctypes.c_double), ("ms_cull", ctypes.c_double),
-                ("ms_raster", ctypes.c_double), ("ms_resolve", ctypes.c_double),
+                ("ms_raster", ctypes.c_double), ("ms_shade", ctypes.c_double),
+                ("ms_resolve", ctypes.c_double),
                 ("raster_launches", ctypes.c_uint64)]
 
 

@@ -72,6 +72,7 @@ Slot::~Slot() {
     cudaFree(scratch.counters);
     cudaFree(scratch.stats);
     cudaFree(scratch.lod_sel);
+    cudaFree(hqs_accum);
     cudaFree(host_vis);
     cudaFree(host_rgba);
 }
@@ -104,6 +105,35 @@ pc_status Ctx::ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes) {
         if (e != cudaSuccess) return cuda_fail(e, "lod selection");
         s.lod_capacity = nodes;
     }
+    return PC_OK;
+}
+
+// 64-bit words of one view's region of the shading sum buffer (a whole
+// number of 16-byte words).
+static uint64_t hqs_region_words(const pc_view& v) {
+    const uint64_t w = (uint64_t)v.width * v.height * hqs_words(v.flags);
+    return (w + 1) & ~1ull;
+}
+
+// The shading sum buffer holds the regions of every view of the largest
+// launch group of a render call.
+pc_status Ctx::ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews) {
+    const uint32_t maxv = views_per_launch();
+    uint64_t need = 0;
+    for (uint32_t base = 0; base < nviews; base += maxv) {
+        uint64_t group = 0;
+        for (uint32_t j = base; j < std::min(nviews, base + maxv); ++j)
+            group += hqs_region_words(views[j]);
+        need = std::max(need, group);
+    }
+    if (need <= s.hqs_capacity) return PC_OK;
+    cudaStreamSynchronize(s.stream);
+    cudaFree(s.hqs_accum);
+    s.hqs_accum = nullptr;
+    s.hqs_capacity = 0;
+    cudaError_t e = cudaMalloc(&s.hqs_accum, need * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e, "shading sum buffer");
+    s.hqs_capacity = need;
     return PC_OK;
 }
 
@@ -153,6 +183,8 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
     const CloudView cv = cl.view();
     const uint32_t maxv = views_per_launch();
     for (uint32_t base = 0; base < nviews; base += maxv) {
+        uint64_t accum_off = 0;
+        bool shade = false;
         ViewTable vt;
         std::memset(&vt, 0, sizeof vt);
         vt.n = std::min(maxv, nviews - base);
@@ -169,6 +201,16 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
             p.lod_px_periphery = pv.lod_px_periphery;
             p.vis = fbs[base + j].vis;
             p.rgba = fbs[base + j].rgba;
+            if (hqs_words(pv.flags)) {
+                if (accum_off + hqs_region_words(pv) > slot->hqs_capacity) {
+                    fail_msg("view %u: shading sum buffer too small for its launch group",
+                             base + j);
+                    return PC_EINVAL;
+                }
+                p.accum = slot->hqs_accum + accum_off;
+                accum_off += hqs_region_words(pv);
+                shade = true;
+            }
         }
         FrameEvents* fe = nullptr;
         if (timing_on) {
@@ -192,9 +234,15 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
         e = launch_raster(cv, vt, base, slot->scratch, shape_for(vt.n), st);
         if (e != cudaSuccess) return cuda_fail(e, "raster launch");
         if (fe) cudaEventRecord(fe->ev[3], st);
+        if (shade) {
+            e = launch_shade(cv, vt, base, slot->scratch, shape_for(vt.n), st);
+            if (e != cudaSuccess) return cuda_fail(e, "shading launch");
+            launches += 1;
+        }
+        if (fe) cudaEventRecord(fe->ev[4], st);
         e = launch_resolve(cv, vt, slot->scratch, st);
         if (e != cudaSuccess) return cuda_fail(e, "resolve launch");
-        if (fe) cudaEventRecord(fe->ev[4], st);
+        if (fe) cudaEventRecord(fe->ev[5], st);
         launches += 4;
         raster_launches += 1;
     }
@@ -225,6 +273,7 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
     if (!slot) slot = slot_for(st);
     std::lock_guard<std::mutex> sg(slot->mu);
     pc_status rc = ensure_capacity(*slot, cl.n_entries, cl.is_lod ? cl.n_batches : 0);
+    if (rc == PC_OK) rc = ensure_hqs(*slot, views, nviews);
     if (rc != PC_OK) return rc;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
@@ -244,7 +293,10 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
         }
         if (e != cudaSuccess) return cuda_fail(e, "graph capture");
         const uint32_t maxv = views_per_launch();
-        const uint64_t key = ((uint64_t)nviews << 8) | maxv | ((uint64_t)cl.is_lod << 40);
+        uint64_t shaded = 0;   // the views with a colour pass change the launch layout
+        for (uint32_t v = 0; v < nviews; ++v) shaded |= (uint64_t)(hqs_words(views[v].flags) != 0);
+        const uint64_t key = ((uint64_t)nviews << 8) | maxv | ((uint64_t)cl.is_lod << 40) |
+                             (shaded << 41);
         cudaGraphExec_t& exec = slot->graphs[key];
         if (exec) {
             cudaGraphExecUpdateResultInfo info;
@@ -633,8 +685,8 @@ pc_status pc_get_view_stats(pc_ctx* h, void* stream, uint32_t view, pc_view_stat
         out->points_processed += out->points_k[k];
     }
     out->words_loaded_bytes = 4ull * st[S_WORDS];
-    out->points_accepted = st[S_ACCEPTED];
     out->points_atomic = st[S_ATOMICS];
+    out->points_blended = st[S_BLENDED];
     return ctx->check_device_error(*slot);
 }
 
@@ -660,13 +712,14 @@ pc_status pc_timing_end(pc_ctx* h, pc_timing* out) {
     std::lock_guard<std::mutex> g(ctx->mu);
     std::memset(out, 0, sizeof *out);
     for (auto& fe : ctx->frame_events) {
-        if (cudaEventSynchronize(fe.ev[4]) != cudaSuccess) return PC_ECUDA;
-        float t[4];
-        for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], fe.ev[i], fe.ev[i + 1]);
+        if (cudaEventSynchronize(fe.ev[5]) != cudaSuccess) return PC_ECUDA;
+        float t[5];
+        for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], fe.ev[i], fe.ev[i + 1]);
         out->ms_clear += t[0];
         out->ms_cull += t[1];
         out->ms_raster += t[2];
-        out->ms_resolve += t[3];
+        out->ms_shade += t[3];
+        out->ms_resolve += t[4];
         out->frames += 1;
     }
     out->launches = (uint32_t)ctx->launches;

@@ -46,6 +46,8 @@ struct Slot {
     std::mutex mu;
     Scratch scratch{};
     uint64_t lod_capacity = 0;      // nodes the LOD selection buffer holds
+    unsigned long long* hqs_accum = nullptr;   // high-quality shading sums of a launch group
+    uint64_t hqs_capacity = 0;      // 64-bit words hqs_accum holds
     uint64_t* host_vis = nullptr;     // pc_render_host framebuffers
     uint32_t* host_rgba = nullptr;
     uint64_t host_pixels = 0;
@@ -63,7 +65,7 @@ struct Tune {
 };
 
 struct FrameEvents {
-    cudaEvent_t ev[5];   // start, after clear, after cull, after raster, after resolve
+    cudaEvent_t ev[6];   // start, after clear, cull, raster, shade (colour pass), resolve
 };
 
 struct ServeState;   // serve.cpp
@@ -93,6 +95,7 @@ struct Ctx {
     Slot* slot_for(cudaStream_t st);
     std::shared_ptr<Cloud> find_cloud(pc_cloud h);
     pc_status ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes);
+    pc_status ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews);
     RasterShape shape_for(uint32_t nviews);
     uint32_t seg_points_for(uint32_t nviews) const;
     uint32_t views_per_launch() const;

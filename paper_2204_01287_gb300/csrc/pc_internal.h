@@ -23,6 +23,7 @@ enum : uint32_t {
     C_GRAB = 1,      // entries taken by raster warps
     C_ERROR = 2,     // device error flag (nonzero = error code)
     C_ERRINFO = 3,   // first offending value
+    C_GRAB_SHADE = 4,  // entries taken by high-quality shading warps
     C_COUNT = 8
 };
 
@@ -32,8 +33,8 @@ enum : uint32_t {
     S_BK1 = 1,       // ... with k = 1, 2, 3
     S_PK1 = 4,       // their points with k = 1, 2, 3
     S_WORDS = 7,     // coordinate words loaded for this view's launch group
-    S_ACCEPTED = 8,  // points that landed inside the viewport
     S_ATOMICS = 9,   // points that passed the early-depth test and issued atomicMin
+    S_BLENDED = 10,  // high-quality shading: points summed into their pixel
     S_COUNT = 16
 };
 
@@ -43,6 +44,7 @@ enum : uint32_t {
     E_ENTRY_RANGE = 1,     // draw-list overflow
     E_BATCH_RANGE = 2,     // batch outside the point buffers
     E_INDEX_RANGE = 3,     // visibility key with an index outside the cloud
+    E_HQS_OVERFLOW = 4,    // a pixel's colour sums exceeded their field width
 };
 
 // One view as the kernels see it (passed by value in a ViewTable).
@@ -55,7 +57,17 @@ struct ViewParams {
     uint32_t pad;
     uint64_t* vis;        // device, width*height
     uint32_t* rgba;       // device, width*height, may be null
+    unsigned long long* accum;  // high-quality shading sums (library scratch), else null
 };
+
+// Words of the high-quality shading sum buffer per pixel of a view: 2 (R | G << 32,
+// B | n << 32), 1 packed (R | G << 16 | B << 32 | n << 48), 0 without shading.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t hqs_words(uint32_t flags) {
+    return (flags & PC_VIEW_HQS_PACKED) ? 1u : (flags & PC_VIEW_HQS) ? 2u : 0u;
+}
 
 // Up to kMaxViewsPerLaunch views; lives in the kernel parameter space so that
 // launches need no host->device copy and can be captured in CUDA graphs.
@@ -117,6 +129,10 @@ cudaError_t launch_cull(const CloudView& c, const ViewTable& vt, uint32_t view_b
 cudaError_t launch_lod_pass(const CloudView& c, const ViewTable& vt, Scratch s, cudaStream_t st);
 cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                           Scratch s, RasterShape shape, cudaStream_t st);
+// High-quality shading colour pass (Sec. 3.6) over the draw list of the
+// launch, for the views with a sum buffer; after launch_raster.
+cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_base, Scratch s,
+                         RasterShape shape, cudaStream_t st);
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s,
                            cudaStream_t st);
 // Blocks per SM the raster kernel can keep resident at a block size.

@@ -52,6 +52,16 @@ __global__ void k_clear(ViewTable vt, uint32_t view_base, Scratch s) {
          i += (uint64_t)gridDim.x * blockDim.x)
         p2[i] = ones;
     if ((npix & 1) && blockIdx.x == 0 && threadIdx.x == 0) vp.vis[npix - 1] = ~0ull;
+    if (vp.accum) {
+        // high-quality shading sums <- 0; each view's region is a whole number
+        // of 16-byte words
+        ulonglong2* a2 = reinterpret_cast<ulonglong2*>(vp.accum);
+        const uint64_t na = (npix * hqs_words(vp.flags) + 1) / 2;
+        const ulonglong2 zero = make_ulonglong2(0ull, 0ull);
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            a2[i] = zero;
+    }
 }
 
 // ---- k_cull: Sec. 3.2 culling and Sec. 3.3 precision ----------------------------
@@ -628,6 +638,172 @@ __global__ void __launch_bounds__(kRasterThreads) k_rasterN(CloudView c, ViewTab
                       (unsigned long long)sh_atom[i]);
 }
 
+// ---- k_shade: Sec. 3.6 high-quality shading, colour pass ---------------------------
+//
+// Walks the same draw list as the depth pass (same segments, same precision per
+// view), so every point it projects was drawn by the depth pass and its pixel
+// holds the closest depth w_min. A point adds its colour to the pixel's sums
+// when w <= fl(w_min * 1.01f). Consecutive points of a group that land on the
+// same pixel are summed in registers first; integer sums do not depend on the
+// order of the additions, so the result is exact.
+
+constexpr uint32_t kHqsMaxCount = 16843009u;   // largest n with 255 n < 2^32
+constexpr uint32_t kHqsMaxCountPacked = 257u;  // largest n with 255 n < 2^16
+
+template <bool PACKED>
+__device__ __forceinline__ void hqs_add(const Scratch& s, unsigned long long* accum, uint32_t pix,
+                                        uint32_t r, uint32_t g, uint32_t b, uint32_t n) {
+    if (PACKED) {
+        const unsigned long long add = (unsigned long long)r | ((unsigned long long)g << 16) |
+                                       ((unsigned long long)b << 32) |
+                                       ((unsigned long long)n << 48);
+        const unsigned long long old = atomicAdd(accum + pix, add);
+        if ((uint32_t)(old >> 48) + n > kHqsMaxCountPacked) raise_error(s, E_HQS_OVERFLOW, pix);
+    } else {
+        atomicAdd(accum + 2ull * pix, (unsigned long long)r | ((unsigned long long)g << 32));
+        const unsigned long long old =
+            atomicAdd(accum + 2ull * pix + 1, (unsigned long long)b | ((unsigned long long)n << 32));
+        if ((uint32_t)(old >> 32) + n > kHqsMaxCount) raise_error(s, E_HQS_OVERFLOW, pix);
+    }
+}
+
+template <bool PARTIAL, bool PACKED, bool STREAM>
+__device__ __forceinline__ uint32_t shade_quad(const Scratch& s, const CloudView& c,
+                                               const ViewConst& vc, unsigned long long* accum,
+                                               const float (&x)[4], const float (&y)[4],
+                                               const float (&z)[4], uint32_t idx0,
+                                               uint32_t valid) {
+    uint32_t pix[4], w[4];
+    bool live[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float cx = clip_row4(vc.mx, x[j], y[j], z[j]);
+        const float cy = clip_row4(vc.my, x[j], y[j], z[j]);
+        const float cw = clip_row4(vc.mw, x[j], y[j], z[j]);
+        live[j] = cw > 0.0f;
+        if (PARTIAL) live[j] = live[j] && ((valid >> j) & 1u);
+        uint32_t bx = 0, by = 0;
+        if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
+        const uint32_t px = bx - 0x4B000000u, py = by - 0x4B000000u;
+        live[j] = live[j] && px < vc.width && py < vc.height;
+        w[j] = __float_as_uint(cw);
+        pix[j] = py * vc.width + px;
+    }
+    uint32_t wmin[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wmin[j] = live[j] ? (uint32_t)(vc.vis[pix[j]] >> 32) : 0u;
+    uint32_t take = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float limit = __fmul_rn(__uint_as_float(wmin[j]), 1.01f);
+        take |= (uint32_t)(live[j] && __uint_as_float(w[j]) <= limit) << j;
+    }
+    if (!take) return 0;
+    const uint4 col = ld_words<STREAM>(c.color + idx0);
+    const uint32_t cc[4] = {col.x, col.y, col.z, col.w};
+    uint32_t r = 0, g = 0, b = 0, n = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!((take >> j) & 1u)) continue;
+        r += cc[j] & 255u;
+        g += (cc[j] >> 8) & 255u;
+        b += (cc[j] >> 16) & 255u;
+        n += 1;
+        // carry the sums to the next point of the group on the same pixel
+        if (j < 3 && ((take >> (j + 1)) & 1u) && pix[j + 1] == pix[j]) continue;
+        hqs_add<PACKED>(s, accum, pix[j], r, g, b, n);
+        r = g = b = n = 0;
+    }
+    return __popc(take);
+}
+
+template <int K, bool STREAM, bool PACKED>
+__device__ __forceinline__ uint32_t shade_segment(const Scratch& s, const CloudView& c,
+                                                  const ViewConst& vc, unsigned long long* accum,
+                                                  const DecConst& d, uint32_t p0, uint32_t p1,
+                                                  uint32_t lane) {
+    uint32_t n_blend = 0;
+    for (uint32_t base = p0 & ~3u; base < p1; base += 128u) {
+        const uint32_t g = base + 4u * lane;
+        if (g >= p1) continue;
+        const uint4 q1 = ld_words<STREAM>(c.w1 + g);
+        uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
+        if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
+        if (K >= 3) q3 = ld_words<STREAM>(c.w3 + g);
+        float x[4], y[4], z[4];
+        decode_point<K>(d, q1.x, q2.x, q3.x, x[0], y[0], z[0]);
+        decode_point<K>(d, q1.y, q2.y, q3.y, x[1], y[1], z[1]);
+        decode_point<K>(d, q1.z, q2.z, q3.z, x[2], y[2], z[2]);
+        decode_point<K>(d, q1.w, q2.w, q3.w, x[3], y[3], z[3]);
+        if (g >= p0 && g + 4u <= p1) {
+            n_blend += shade_quad<false, PACKED, STREAM>(s, c, vc, accum, x, y, z, g, 0xFu);
+        } else {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
+            n_blend += shade_quad<true, PACKED, STREAM>(s, c, vc, accum, x, y, z, g, valid);
+        }
+    }
+    return n_blend;
+}
+
+template <bool STREAM, bool PACKED>
+__device__ __forceinline__ uint32_t shade_segment_k(const Scratch& s, const CloudView& c,
+                                                    const ViewConst& vc,
+                                                    unsigned long long* accum, const pc_batch& bt,
+                                                    int k, uint32_t p0, uint32_t p1,
+                                                    uint32_t lane) {
+    const DecConst d = make_dec_const(bt, k);
+    if (k == 1) return shade_segment<1, STREAM, PACKED>(s, c, vc, accum, d, p0, p1, lane);
+    if (k == 2) return shade_segment<2, STREAM, PACKED>(s, c, vc, accum, d, p0, p1, lane);
+    return shade_segment<3, STREAM, PACKED>(s, c, vc, accum, d, p0, p1, lane);
+}
+
+// Persistent warps take draw-list segments (a counter of their own); each
+// segment is walked once per shaded view that did not cull its batch. With one
+// shaded view per launch the loads stream past L1, as in the depth pass.
+// (No __launch_bounds__: with it ptxas held this kernel to 32 registers and
+// spilled.)
+template <bool STREAM>
+__global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s,
+                        uint32_t shade_mask) {
+    __shared__ uint32_t sh_blend[kMaxViewsPerLaunch];
+    for (uint32_t i = threadIdx.x; i < kMaxViewsPerLaunch; i += blockDim.x) sh_blend[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n_entries = s.counters[C_ENTRIES];
+    for (;;) {
+        uint32_t e_idx = 0;
+        if (lane == 0) e_idx = atomicAdd(&s.counters[C_GRAB_SHADE], 1u);
+        e_idx = __shfl_sync(FULL, e_idx, 0);
+        if (e_idx >= n_entries || e_idx >= s.capacity) break;
+        const DrawEntry e = s.entries[e_idx];
+        if (e.batch >= c.n_batches) {
+            if (lane == 0) raise_error(s, E_BATCH_RANGE, e.batch);
+            continue;
+        }
+        const pc_batch bt = c.batches[e.batch];
+        const uint32_t p0 = bt.first + e.seg_first;
+        for (uint32_t mm = e.view_mask & shade_mask; mm; mm &= mm - 1) {
+            const uint32_t v = __ffs(mm) - 1;
+            const ViewConst vc = make_view_const(vt.v[v]);
+            const int k = (int)((e.kcodes >> (2 * v)) & 3u);
+            const uint32_t n = (vt.v[v].flags & PC_VIEW_HQS_PACKED)
+                ? shade_segment_k<STREAM, true>(s, c, vc, vt.v[v].accum, bt, k, p0,
+                                                p0 + e.seg_count, lane)
+                : shade_segment_k<STREAM, false>(s, c, vc, vt.v[v].accum, bt, k, p0,
+                                                 p0 + e.seg_count, lane);
+            const uint32_t t = __reduce_add_sync(FULL, n);
+            if (lane == 0 && t) atomicAdd(&sh_blend[v], t);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < vt.n; i += blockDim.x)
+        if (sh_blend[i])
+            atomicAdd(&s.stats[(uint64_t)(view_base + i) * S_COUNT + S_BLENDED],
+                      (unsigned long long)sh_blend[i]);
+}
+
 // ---- k_resolve ---------------------------------------------------------------------
 
 __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
@@ -637,9 +813,11 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
     if (!vp.rgba) return;
     const uint64_t npix = (uint64_t)vp.width * vp.height;
     const bool dilate = (vp.flags & PC_VIEW_DILATE) != 0;
+    const uint32_t words = vp.accum ? hqs_words(vp.flags) : 0u;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (uint64_t)gridDim.x * blockDim.x) {
         unsigned long long key = vp.vis[p];
+        uint64_t at = p;   // the pixel whose sums a shaded view shows
         if (dilate) {
             // Sec. 3.7: the closest point within (2r+1)^2 pixels, r by ring
             const int px = (int)(p % vp.width), py = (int)(p / vp.width);
@@ -649,12 +827,33 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
             const int y0 = max(py - r, 0), y1 = min(py + r, (int)vp.height - 1);
             for (int y = y0; y <= y1; ++y)
                 for (int x = x0; x <= x1; ++x) {
-                    const unsigned long long k = vp.vis[(uint64_t)y * vp.width + x];
-                    if (k < key) key = k;
+                    const uint64_t q = (uint64_t)y * vp.width + x;
+                    const unsigned long long k = vp.vis[q];
+                    if (k < key) {
+                        key = k;
+                        at = q;
+                    }
                 }
         }
         uint32_t out = 0u;
-        if (key != ~0ull) {
+        if (words && key != ~0ull) {
+            // Sec. 3.6: per-channel average of the sums, rounded down
+            uint32_t r, g, b, n;
+            if (words == 1) {
+                const unsigned long long a = vp.accum[at];
+                r = (uint32_t)(a & 0xFFFFu);
+                g = (uint32_t)((a >> 16) & 0xFFFFu);
+                b = (uint32_t)((a >> 32) & 0xFFFFu);
+                n = (uint32_t)(a >> 48);
+            } else {
+                const ulonglong2 a = reinterpret_cast<const ulonglong2*>(vp.accum)[at];
+                r = (uint32_t)a.x;
+                g = (uint32_t)(a.x >> 32);
+                b = (uint32_t)a.y;
+                n = (uint32_t)(a.y >> 32);
+            }
+            if (n) out = (r / n) | ((g / n) << 8) | ((b / n) << 16) | 0xFF000000u;
+        } else if (key != ~0ull) {
             const uint32_t idx = (uint32_t)key;
             if (idx < c.n_points) out = c.color[idx];
             else raise_error(s, E_INDEX_RANGE, idx);
@@ -721,6 +920,24 @@ cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view
     int blocks = shape.blocks > 0 ? shape.blocks : num_sms() * raster_occupancy(threads, multi);
     if (multi) k_rasterN<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
     else k_raster1<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_base, Scratch s,
+                         RasterShape shape, cudaStream_t st) {
+    uint32_t mask = 0;
+    for (uint32_t v = 0; v < vt.n; ++v)
+        if (vt.v[v].accum && hqs_words(vt.v[v].flags)) mask |= 1u << v;
+    if (!mask) return cudaSuccess;
+    int threads = shape.threads_per_block > 0 ? shape.threads_per_block : kRasterThreads;
+    threads = threads > kRasterThreads ? kRasterThreads : (threads < 32 ? 32 : threads & ~31);
+    const bool stream = (mask & (mask - 1)) == 0;
+    int nb = 0;
+    if (stream) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<true>, threads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<false>, threads, 0);
+    const int blocks = num_sms() * (nb > 0 ? nb : 1);
+    if (stream) k_shade<true><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
+    else k_shade<false><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
     return cudaGetLastError();
 }
 
