@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-lod", action="store_true")
     ap.add_argument("--no-multiview", action="store_true")
     ap.add_argument("--no-order", action="store_true")
+    ap.add_argument("--no-hqs", action="store_true")
     ap.add_argument("--order-points", type=float, default=2e8)
     ap.add_argument("--lod-points", type=float, default=1e9)
     ap.add_argument("--verbose", action="store_true")
@@ -354,6 +355,47 @@ def order_bench(args, pcr, torch, ctx):
     return out
 
 
+def hqs_bench(args, pcr, torch, ctx, cloud, m, plain_ms):
+    """Sec. 3.6 high-quality shading on the main cloud and view: the depth pass,
+    then a colour pass that sums the colours of the points within 1% of the
+    closest depth per pixel, then the averaging resolve. Two variants: two
+    64-bit atomic adds per blended point (32-bit sums), and one (packed 18-bit
+    sums) with a second pass for the pixels that get more than 1023 points.
+    Per-pass times from CUDA events around each launch."""
+    W, H = args.width, args.height
+    out = {"plain_ms_per_frame": plain_ms}
+    for name, flag in (("two_word", pcr.PC_VIEW_HQS), ("packed", pcr.PC_VIEW_HQS_PACKED)):
+        v = pcr.make_view(m, W, H, pcr.PC_VIEW_CULL | flag)
+        fbs = ctx.framebuffers([v])
+        for _ in range(3):
+            ctx.render(cloud, [v], fbs)
+        torch.cuda.synchronize()
+        st = ctx.stats()
+        k = max(20, args.steps // 10)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            ctx.render(cloud, [v], fbs)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        pcr.pc_timing_begin(ctx.h)
+        for _ in range(5):
+            ctx.render(cloud, [v], fbs)
+        t = pcr.pc_timing_end(ctx.h)
+        f = max(1, t.frames)
+        out[name] = {"ms_per_frame": ms, "frames": k, "cost_vs_plain": ms / plain_ms,
+                     "passes_ms": {"clear": t.ms_clear / f, "cull": t.ms_cull / f,
+                                   "depth": t.ms_raster / f, "shade": t.ms_shade / f,
+                                   "resolve": t.ms_resolve / f},
+                     "points_blended_per_frame": st["points_blended"],
+                     "fallback_pixels": st["hqs_fallback_pixels"],
+                     "points_processed_per_frame": st["points_processed"]}
+        del fbs
+    return out
+
+
 def lod_bench(args, pcr, torch, ctx, params):
     """Sec. 3.5 on the terrain: a layered octree of --lod-points points (max 12
     levels, <= 10,240 points per node) rendered along the 120-frame fly-through
@@ -397,6 +439,28 @@ def lod_bench(args, pcr, torch, ctx, params):
                      "batches_rendered_avg": nodes / len(views[::10]),
                      "points_processed_avg": pts / len(views[::10])}
     out["speedup_vs_brute_force"] = out["brute_force"]["ms_per_frame"] / out["lod"]["ms_per_frame"]
+    # LOD with high-quality shading (Sec. 3.5 with Sec. 3.6), both sum layouts
+    for hname, flag in (("lod_hqs_two_word", pcr.PC_VIEW_HQS),
+                        ("lod_hqs_packed", pcr.PC_VIEW_HQS_PACKED)):
+        views = [pcr.make_view(m, W, H, pcr.PC_VIEW_CULL | flag, 300.0) for m in frames]
+        for v in views[:3]:
+            ctx.render(lod, [v], fbs)
+        blended = fallback = 0
+        for v in views[::10]:
+            ctx.render(lod, [v], fbs)
+            st = ctx.stats()
+            blended += st["points_blended"]
+            fallback += st["hqs_fallback_pixels"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for v in views:
+            ctx.render(lod, [v], fbs)
+        e1.record()
+        torch.cuda.synchronize()
+        out[hname] = {"ms_per_frame": e0.elapsed_time(e1) / len(views),
+                      "points_blended_avg": blended / len(views[::10]),
+                      "fallback_pixels_avg": fallback / len(views[::10])}
     pcr.pc_release_cloud(ctx.h, lod)
     pcr.pc_release_cloud(ctx.h, src)
     return out
@@ -571,6 +635,11 @@ def main():
         multiview = multiview_bench(args, pcr, torch, ctx, cloud, params)
         log(args, f"multiview: {multiview}")
 
+    hqs = None
+    if not args.no_hqs:
+        hqs = hqs_bench(args, pcr, torch, ctx, cloud, m, ms_per_frame)
+        log(args, f"hqs: {hqs}")
+
     order = None
     if not args.no_order:
         order = order_bench(args, pcr, torch, ctx)
@@ -601,7 +670,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "setup_s": {"generate": t_gen, "encode_upload": t_up}},
                 "roofline": roofline, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
-                "multiview": multiview, "serving": serving, "lod": lod,
+                "multiview": multiview, "serving": serving, "lod": lod, "hqs": hqs,
                 "vertex_order": order, "autotune": tune,
                 "gpu_launches": int(timing.launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -199,15 +199,18 @@ pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
 #define PC_VIEW_HQS            0x80u       /* high-quality shading (Sec. 3.6): after the depth pass
                                               a colour pass sums R, G, B and a count per pixel over
                                               the points with w <= fl(w_min * 1.01f), two 64-bit
-                                              atomicAdds per point (32-bit sums, exact up to
-                                              16,843,009 points per pixel), and the resolve
-                                              writes the per-channel average (rounded down) with
-                                              alpha 255 */
-#define PC_VIEW_HQS_PACKED     0x100u      /* the same with one 64-bit atomicAdd per point (16-bit
-                                              sums, exact up to 257 points per pixel within the
-                                              window, the case of LOD clouds); a pixel that gets
-                                              more raises the device error flag (PC_EDEVICE). Set
-                                              alone or with PC_VIEW_HQS; takes precedence */
+                                              atomic adds per point into 32-bit sums, and the
+                                              resolve writes the per-channel average (rounded
+                                              down) with alpha 255. Exact up to 16,843,009 points
+                                              per pixel; beyond, the resolve raises the device
+                                              error flag (PC_EDEVICE) */
+#define PC_VIEW_HQS_PACKED     0x100u      /* the same with one 64-bit atomic add per point into
+                                              18-bit sums and a 10-bit count; a pixel that gets
+                                              more than 1023 points is summed again by a second
+                                              pass with two atomics per point, so the image is
+                                              exact in every case (the second pass returns at
+                                              once when no pixel overflowed). Set alone or with
+                                              PC_VIEW_HQS; takes precedence */
 
 typedef struct {
     float    view_proj[16];   /* world -> clip, column-major */
@@ -225,7 +228,7 @@ typedef struct {
  * and rgba[width*height] (R | G<<8 | B<<16 | A<<24, 0 where no point landed).
  * rgba may be NULL to skip the resolve. Both 16-byte aligned. Views with
  * PC_VIEW_HQS or PC_VIEW_HQS_PACKED also use a per-pixel sum buffer (16 or
- * 8 bytes per pixel) that the library owns, one per stream, sized to the
+ * 32 bytes per pixel) that the library owns, one per stream, sized to the
  * largest launch group of views seen. */
 typedef struct {
     uint64_t* vis;
@@ -285,6 +288,7 @@ typedef struct {
     uint64_t words_loaded_bytes;   /* coordinate bytes the raster launch loaded for this view */
     uint64_t points_atomic;        /* points that issued atomicMin (Table 2 "rendered points") */
     uint64_t points_blended;       /* high-quality shading: points summed into a pixel */
+    uint64_t hqs_fallback_pixels;  /* PC_VIEW_HQS_PACKED: pixels summed by the second pass */
 } pc_view_stats;
 
 pc_status pc_get_view_stats(pc_ctx* ctx, void* stream, uint32_t view, pc_view_stats* out);

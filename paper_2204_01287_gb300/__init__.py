@@ -75,7 +75,7 @@ class pc_view_stats(ctypes.Structure):
                 ("points_processed", ctypes.c_uint64),
                 ("words_loaded_bytes", ctypes.c_uint64),
                 ("points_atomic", ctypes.c_uint64),
-                ("points_blended", ctypes.c_uint64)]
+                ("points_blended", ctypes.c_uint64), ("hqs_fallback_pixels", ctypes.c_uint64)]
 
     def as_dict(self):
         return {"batches_total": self.batches_total, "batches_rendered": self.batches_rendered,
@@ -83,7 +83,8 @@ class pc_view_stats(ctypes.Structure):
                 "points_processed": self.points_processed,
                 "words_loaded_bytes": self.words_loaded_bytes,
                 "points_atomic": self.points_atomic,
-                "points_blended": self.points_blended}
+                "points_blended": self.points_blended,
+                "hqs_fallback_pixels": self.hqs_fallback_pixels}
 
 
 class pc_timing(ctypes.Structure):

@@ -235,9 +235,10 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
         if (e != cudaSuccess) return cuda_fail(e, "raster launch");
         if (fe) cudaEventRecord(fe->ev[3], st);
         if (shade) {
-            e = launch_shade(cv, vt, base, slot->scratch, shape_for(vt.n), st);
+            int nk = 0;
+            e = launch_shade(cv, vt, base, slot->scratch, shape_for(vt.n), st, &nk);
             if (e != cudaSuccess) return cuda_fail(e, "shading launch");
-            launches += 1;
+            launches += nk;
         }
         if (fe) cudaEventRecord(fe->ev[4], st);
         e = launch_resolve(cv, vt, slot->scratch, st);
@@ -687,6 +688,7 @@ pc_status pc_get_view_stats(pc_ctx* h, void* stream, uint32_t view, pc_view_stat
     out->words_loaded_bytes = 4ull * st[S_WORDS];
     out->points_atomic = st[S_ATOMICS];
     out->points_blended = st[S_BLENDED];
+    out->hqs_fallback_pixels = st[S_FALLBACK];
     return ctx->check_device_error(*slot);
 }
 

@@ -24,6 +24,7 @@ enum : uint32_t {
     C_ERROR = 2,     // device error flag (nonzero = error code)
     C_ERRINFO = 3,   // first offending value
     C_GRAB_SHADE = 4,  // entries taken by high-quality shading warps
+    C_GRAB_FALLBACK = 5,  // ... by the second pass of packed shading
     C_COUNT = 8
 };
 
@@ -35,6 +36,7 @@ enum : uint32_t {
     S_WORDS = 7,     // coordinate words loaded for this view's launch group
     S_ATOMICS = 9,   // points that passed the early-depth test and issued atomicMin
     S_BLENDED = 10,  // high-quality shading: points summed into their pixel
+    S_FALLBACK = 11, // packed shading: pixels that overflowed into the two-word sums
     S_COUNT = 16
 };
 
@@ -61,12 +63,13 @@ struct ViewParams {
 };
 
 // Words of the high-quality shading sum buffer per pixel of a view: 2 (R | G << 32,
-// B | n << 32), 1 packed (R | G << 16 | B << 32 | n << 48), 0 without shading.
+// B | n << 32); packed 4 (R | G << 18 | B << 36 | n << 54, fallback flag, and the
+// two-word sums of a pixel that overflowed); 0 without shading.
 #ifdef __CUDACC__
 __host__ __device__
 #endif
 inline uint32_t hqs_words(uint32_t flags) {
-    return (flags & PC_VIEW_HQS_PACKED) ? 1u : (flags & PC_VIEW_HQS) ? 2u : 0u;
+    return (flags & PC_VIEW_HQS_PACKED) ? 4u : (flags & PC_VIEW_HQS) ? 2u : 0u;
 }
 
 // Up to kMaxViewsPerLaunch views; lives in the kernel parameter space so that
@@ -130,9 +133,10 @@ cudaError_t launch_lod_pass(const CloudView& c, const ViewTable& vt, Scratch s, 
 cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                           Scratch s, RasterShape shape, cudaStream_t st);
 // High-quality shading colour pass (Sec. 3.6) over the draw list of the
-// launch, for the views with a sum buffer; after launch_raster.
+// launch, for the views with a sum buffer, and the fallback pass of packed
+// views; after launch_raster. *launched: kernels launched.
 cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_base, Scratch s,
-                         RasterShape shape, cudaStream_t st);
+                         RasterShape shape, cudaStream_t st, int* launched);
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s,
                            cudaStream_t st);
 // Blocks per SM the raster kernel can keep resident at a block size.

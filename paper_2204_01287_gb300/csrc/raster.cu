@@ -646,32 +646,50 @@ __global__ void __launch_bounds__(kRasterThreads) k_rasterN(CloudView c, ViewTab
 // when w <= fl(w_min * 1.01f). Consecutive points of a group that land on the
 // same pixel are summed in registers first; integer sums do not depend on the
 // order of the additions, so the result is exact.
+//
+// Sum layouts per pixel (64-bit words):
+//   two-word  [R | G << 32, B | n << 32]: two reductions per addition, no
+//             returned value; exact while n <= 16,843,009 (255 n < 2^32), which
+//             the resolve checks: a carry out of the B field needs a larger n,
+//             and n itself cannot wrap (a point is counted once).
+//   packed    [R | G << 18 | B << 36 | n << 54, fallback flag, two-word sums]:
+//             one atomicAdd per addition, exact while n <= 1023 (255 n < 2^18).
+//             The addition that takes n past 1023 sees the exact old value (the
+//             fields hold every earlier addition) and flags the pixel; a second
+//             pass then sums every point of the flagged pixels into the
+//             two-word sums, which the resolve uses there.
 
 constexpr uint32_t kHqsMaxCount = 16843009u;   // largest n with 255 n < 2^32
-constexpr uint32_t kHqsMaxCountPacked = 257u;  // largest n with 255 n < 2^16
+constexpr uint32_t kHqsPackedMax = 1023u;      // largest n with 255 n < 2^18 and n < 2^10
 
-template <bool PACKED>
-__device__ __forceinline__ void hqs_add(const Scratch& s, unsigned long long* accum, uint32_t pix,
-                                        uint32_t r, uint32_t g, uint32_t b, uint32_t n) {
-    if (PACKED) {
-        const unsigned long long add = (unsigned long long)r | ((unsigned long long)g << 16) |
-                                       ((unsigned long long)b << 32) |
-                                       ((unsigned long long)n << 48);
-        const unsigned long long old = atomicAdd(accum + pix, add);
-        if ((uint32_t)(old >> 48) + n > kHqsMaxCountPacked) raise_error(s, E_HQS_OVERFLOW, pix);
+enum class ShadeMode { kTwoWord, kPacked, kFallback };
+
+template <ShadeMode MODE>
+__device__ __forceinline__ void hqs_add(unsigned long long* a, uint32_t pix, uint32_t r,
+                                        uint32_t g, uint32_t b, uint32_t n,
+                                        unsigned long long* fallback_pixels) {
+    if (MODE == ShadeMode::kTwoWord) {
+        atomicAdd(a + 2ull * pix, (unsigned long long)r | ((unsigned long long)g << 32));
+        atomicAdd(a + 2ull * pix + 1, (unsigned long long)b | ((unsigned long long)n << 32));
+    } else if (MODE == ShadeMode::kFallback) {
+        atomicAdd(a + 4ull * pix + 2, (unsigned long long)r | ((unsigned long long)g << 32));
+        atomicAdd(a + 4ull * pix + 3, (unsigned long long)b | ((unsigned long long)n << 32));
     } else {
-        atomicAdd(accum + 2ull * pix, (unsigned long long)r | ((unsigned long long)g << 32));
-        const unsigned long long old =
-            atomicAdd(accum + 2ull * pix + 1, (unsigned long long)b | ((unsigned long long)n << 32));
-        if ((uint32_t)(old >> 32) + n > kHqsMaxCount) raise_error(s, E_HQS_OVERFLOW, pix);
+        const unsigned long long add = (unsigned long long)r | ((unsigned long long)g << 18) |
+                                       ((unsigned long long)b << 36) |
+                                       ((unsigned long long)n << 54);
+        const unsigned long long old = atomicAdd(a + 4ull * pix, add);
+        if ((uint32_t)(old >> 54) + n > kHqsPackedMax &&
+            atomicExch(a + 4ull * pix + 1, 1ull) == 0ull)
+            atomicAdd(fallback_pixels, 1ull);
     }
 }
 
-template <bool PARTIAL, bool PACKED, bool STREAM>
-__device__ __forceinline__ uint32_t shade_quad(const Scratch& s, const CloudView& c,
-                                               const ViewConst& vc, unsigned long long* accum,
+template <bool PARTIAL, ShadeMode MODE>
+__device__ __forceinline__ uint32_t shade_quad(const ViewConst& vc, unsigned long long* accum,
+                                               unsigned long long* fallback_pixels,
                                                const float (&x)[4], const float (&y)[4],
-                                               const float (&z)[4], uint32_t idx0,
+                                               const float (&z)[4], const uint4& col,
                                                uint32_t valid) {
     uint32_t pix[4], w[4];
     bool live[4];
@@ -690,16 +708,22 @@ __device__ __forceinline__ uint32_t shade_quad(const Scratch& s, const CloudView
         pix[j] = py * vc.width + px;
     }
     uint32_t wmin[4];
+    unsigned long long flag[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) wmin[j] = live[j] ? (uint32_t)(vc.vis[pix[j]] >> 32) : 0u;
+    for (int j = 0; j < 4; ++j) {
+        // the depth word of the pixel's key (the upper half of the 64-bit key)
+        wmin[j] = live[j] ? reinterpret_cast<const uint32_t*>(vc.vis)[2ull * pix[j] + 1] : 0u;
+        if (MODE == ShadeMode::kFallback) flag[j] = live[j] ? accum[4ull * pix[j] + 1] : 0ull;
+    }
     uint32_t take = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const float limit = __fmul_rn(__uint_as_float(wmin[j]), 1.01f);
-        take |= (uint32_t)(live[j] && __uint_as_float(w[j]) <= limit) << j;
+        bool t = live[j] && __uint_as_float(w[j]) <= limit;
+        if (MODE == ShadeMode::kFallback) t = t && flag[j] != 0ull;
+        take |= (uint32_t)t << j;
     }
     if (!take) return 0;
-    const uint4 col = ld_words<STREAM>(c.color + idx0);
     const uint32_t cc[4] = {col.x, col.y, col.z, col.w};
     uint32_t r = 0, g = 0, b = 0, n = 0;
 #pragma unroll
@@ -711,15 +735,19 @@ __device__ __forceinline__ uint32_t shade_quad(const Scratch& s, const CloudView
         n += 1;
         // carry the sums to the next point of the group on the same pixel
         if (j < 3 && ((take >> (j + 1)) & 1u) && pix[j + 1] == pix[j]) continue;
-        hqs_add<PACKED>(s, accum, pix[j], r, g, b, n);
+        hqs_add<MODE>(accum, pix[j], r, g, b, n, fallback_pixels);
         r = g = b = n = 0;
     }
-    return __popc(take);
+    return MODE == ShadeMode::kFallback ? 0u : (uint32_t)__popc(take);
 }
 
-template <int K, bool STREAM, bool PACKED>
-__device__ __forceinline__ uint32_t shade_segment(const Scratch& s, const CloudView& c,
-                                                  const ViewConst& vc, unsigned long long* accum,
+// Points [p0, p1) of one batch for one shaded view at precision K; the colour
+// words are loaded with the coordinate words (nearly every point of a dense
+// view falls within its pixel's window).
+template <int K, bool STREAM, ShadeMode MODE>
+__device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const ViewConst& vc,
+                                                  unsigned long long* accum,
+                                                  unsigned long long* fallback_pixels,
                                                   const DecConst& d, uint32_t p0, uint32_t p1,
                                                   uint32_t lane) {
     uint32_t n_blend = 0;
@@ -730,51 +758,64 @@ __device__ __forceinline__ uint32_t shade_segment(const Scratch& s, const CloudV
         uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
         if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
         if (K >= 3) q3 = ld_words<STREAM>(c.w3 + g);
+        const uint4 col = ld_words<STREAM>(c.color + g);
         float x[4], y[4], z[4];
         decode_point<K>(d, q1.x, q2.x, q3.x, x[0], y[0], z[0]);
         decode_point<K>(d, q1.y, q2.y, q3.y, x[1], y[1], z[1]);
         decode_point<K>(d, q1.z, q2.z, q3.z, x[2], y[2], z[2]);
         decode_point<K>(d, q1.w, q2.w, q3.w, x[3], y[3], z[3]);
         if (g >= p0 && g + 4u <= p1) {
-            n_blend += shade_quad<false, PACKED, STREAM>(s, c, vc, accum, x, y, z, g, 0xFu);
+            n_blend += shade_quad<false, MODE>(vc, accum, fallback_pixels, x, y, z, col, 0xFu);
         } else {
             uint32_t valid = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
-            n_blend += shade_quad<true, PACKED, STREAM>(s, c, vc, accum, x, y, z, g, valid);
+            n_blend += shade_quad<true, MODE>(vc, accum, fallback_pixels, x, y, z, col, valid);
         }
     }
     return n_blend;
 }
 
-template <bool STREAM, bool PACKED>
-__device__ __forceinline__ uint32_t shade_segment_k(const Scratch& s, const CloudView& c,
-                                                    const ViewConst& vc,
-                                                    unsigned long long* accum, const pc_batch& bt,
-                                                    int k, uint32_t p0, uint32_t p1,
-                                                    uint32_t lane) {
+template <bool STREAM, ShadeMode MODE>
+__device__ __forceinline__ uint32_t shade_segment_k(const CloudView& c, const ViewConst& vc,
+                                                    unsigned long long* accum,
+                                                    unsigned long long* fallback_pixels,
+                                                    const pc_batch& bt, int k, uint32_t p0,
+                                                    uint32_t p1, uint32_t lane) {
     const DecConst d = make_dec_const(bt, k);
-    if (k == 1) return shade_segment<1, STREAM, PACKED>(s, c, vc, accum, d, p0, p1, lane);
-    if (k == 2) return shade_segment<2, STREAM, PACKED>(s, c, vc, accum, d, p0, p1, lane);
-    return shade_segment<3, STREAM, PACKED>(s, c, vc, accum, d, p0, p1, lane);
+    if (k == 1) return shade_segment<1, STREAM, MODE>(c, vc, accum, fallback_pixels, d, p0, p1, lane);
+    if (k == 2) return shade_segment<2, STREAM, MODE>(c, vc, accum, fallback_pixels, d, p0, p1, lane);
+    return shade_segment<3, STREAM, MODE>(c, vc, accum, fallback_pixels, d, p0, p1, lane);
 }
 
 // Persistent warps take draw-list segments (a counter of their own); each
 // segment is walked once per shaded view that did not cull its batch. With one
 // shaded view per launch the loads stream past L1, as in the depth pass.
+// FALLBACK: the second pass for packed views, which returns at once unless
+// one of its views flagged a pixel.
 // (No __launch_bounds__: with it ptxas held this kernel to 32 registers and
 // spilled.)
-template <bool STREAM>
+template <bool STREAM, bool FALLBACK>
 __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s,
                         uint32_t shade_mask) {
     __shared__ uint32_t sh_blend[kMaxViewsPerLaunch];
+    if (FALLBACK) {
+        uint32_t fb = 0;
+        for (uint32_t mm = shade_mask; mm; mm &= mm - 1) {
+            const uint32_t v = __ffs(mm) - 1;
+            if (s.stats[(uint64_t)(view_base + v) * S_COUNT + S_FALLBACK]) fb |= 1u << v;
+        }
+        if (!fb) return;
+        shade_mask = fb;
+    }
     for (uint32_t i = threadIdx.x; i < kMaxViewsPerLaunch; i += blockDim.x) sh_blend[i] = 0;
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n_entries = s.counters[C_ENTRIES];
+    unsigned int* grab = &s.counters[FALLBACK ? C_GRAB_FALLBACK : C_GRAB_SHADE];
     for (;;) {
         uint32_t e_idx = 0;
-        if (lane == 0) e_idx = atomicAdd(&s.counters[C_GRAB_SHADE], 1u);
+        if (lane == 0) e_idx = atomicAdd(grab, 1u);
         e_idx = __shfl_sync(FULL, e_idx, 0);
         if (e_idx >= n_entries || e_idx >= s.capacity) break;
         const DrawEntry e = s.entries[e_idx];
@@ -788,11 +829,17 @@ __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s
             const uint32_t v = __ffs(mm) - 1;
             const ViewConst vc = make_view_const(vt.v[v]);
             const int k = (int)((e.kcodes >> (2 * v)) & 3u);
-            const uint32_t n = (vt.v[v].flags & PC_VIEW_HQS_PACKED)
-                ? shade_segment_k<STREAM, true>(s, c, vc, vt.v[v].accum, bt, k, p0,
-                                                p0 + e.seg_count, lane)
-                : shade_segment_k<STREAM, false>(s, c, vc, vt.v[v].accum, bt, k, p0,
-                                                 p0 + e.seg_count, lane);
+            unsigned long long* fbp = &s.stats[(uint64_t)(view_base + v) * S_COUNT + S_FALLBACK];
+            uint32_t n;
+            if (FALLBACK)
+                n = shade_segment_k<STREAM, ShadeMode::kFallback>(
+                    c, vc, vt.v[v].accum, fbp, bt, k, p0, p0 + e.seg_count, lane);
+            else if (vt.v[v].flags & PC_VIEW_HQS_PACKED)
+                n = shade_segment_k<STREAM, ShadeMode::kPacked>(
+                    c, vc, vt.v[v].accum, fbp, bt, k, p0, p0 + e.seg_count, lane);
+            else
+                n = shade_segment_k<STREAM, ShadeMode::kTwoWord>(
+                    c, vc, vt.v[v].accum, fbp, bt, k, p0, p0 + e.seg_count, lane);
             const uint32_t t = __reduce_add_sync(FULL, n);
             if (lane == 0 && t) atomicAdd(&sh_blend[v], t);
         }
@@ -838,19 +885,27 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
         uint32_t out = 0u;
         if (words && key != ~0ull) {
             // Sec. 3.6: per-channel average of the sums, rounded down
+            const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(vp.accum);
             uint32_t r, g, b, n;
-            if (words == 1) {
-                const unsigned long long a = vp.accum[at];
-                r = (uint32_t)(a & 0xFFFFu);
-                g = (uint32_t)((a >> 16) & 0xFFFFu);
-                b = (uint32_t)((a >> 32) & 0xFFFFu);
-                n = (uint32_t)(a >> 48);
+            ulonglong2 two;   // two-word sums
+            bool use_two = words == 2;
+            if (words == 2) {
+                two = a2[at];
             } else {
-                const ulonglong2 a = reinterpret_cast<const ulonglong2*>(vp.accum)[at];
-                r = (uint32_t)a.x;
-                g = (uint32_t)(a.x >> 32);
-                b = (uint32_t)a.y;
-                n = (uint32_t)(a.y >> 32);
+                const ulonglong2 head = a2[2 * at];   // packed sums, fallback flag
+                use_two = head.y != 0ull;
+                if (use_two) two = a2[2 * at + 1];
+                r = (uint32_t)(head.x & 0x3FFFFu);
+                g = (uint32_t)((head.x >> 18) & 0x3FFFFu);
+                b = (uint32_t)((head.x >> 36) & 0x3FFFFu);
+                n = (uint32_t)(head.x >> 54);
+            }
+            if (use_two) {
+                r = (uint32_t)two.x;
+                g = (uint32_t)(two.x >> 32);
+                b = (uint32_t)two.y;
+                n = (uint32_t)(two.y >> 32);
+                if (n > kHqsMaxCount) raise_error(s, E_HQS_OVERFLOW, (uint32_t)at);
             }
             if (n) out = (r / n) | ((g / n) << 8) | ((b / n) << 16) | 0xFF000000u;
         } else if (key != ~0ull) {
@@ -923,22 +978,38 @@ cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view
     return cudaGetLastError();
 }
 
+template <bool STREAM, bool FALLBACK>
+static cudaError_t launch_shade_kernel(const CloudView& c, const ViewTable& vt, uint32_t view_base,
+                                       Scratch s, int threads, uint32_t mask, cudaStream_t st) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<STREAM, FALLBACK>, threads, 0);
+    const int blocks = num_sms() * (nb > 0 ? nb : 1);
+    k_shade<STREAM, FALLBACK><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_base, Scratch s,
-                         RasterShape shape, cudaStream_t st) {
-    uint32_t mask = 0;
-    for (uint32_t v = 0; v < vt.n; ++v)
-        if (vt.v[v].accum && hqs_words(vt.v[v].flags)) mask |= 1u << v;
+                         RasterShape shape, cudaStream_t st, int* launched) {
+    uint32_t mask = 0, packed = 0;
+    for (uint32_t v = 0; v < vt.n; ++v) {
+        if (!vt.v[v].accum || !hqs_words(vt.v[v].flags)) continue;
+        mask |= 1u << v;
+        if (vt.v[v].flags & PC_VIEW_HQS_PACKED) packed |= 1u << v;
+    }
+    *launched = 0;
     if (!mask) return cudaSuccess;
     int threads = shape.threads_per_block > 0 ? shape.threads_per_block : kRasterThreads;
     threads = threads > kRasterThreads ? kRasterThreads : (threads < 32 ? 32 : threads & ~31);
     const bool stream = (mask & (mask - 1)) == 0;
-    int nb = 0;
-    if (stream) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<true>, threads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<false>, threads, 0);
-    const int blocks = num_sms() * (nb > 0 ? nb : 1);
-    if (stream) k_shade<true><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
-    else k_shade<false><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
-    return cudaGetLastError();
+    cudaError_t e = stream ? launch_shade_kernel<true, false>(c, vt, view_base, s, threads, mask, st)
+                           : launch_shade_kernel<false, false>(c, vt, view_base, s, threads, mask, st);
+    *launched = 1;
+    if (e != cudaSuccess || !packed) return e;
+    const bool stream2 = (packed & (packed - 1)) == 0;
+    e = stream2 ? launch_shade_kernel<true, true>(c, vt, view_base, s, threads, packed, st)
+                : launch_shade_kernel<false, true>(c, vt, view_base, s, threads, packed, st);
+    *launched = 2;
+    return e;
 }
 
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s, cudaStream_t st) {

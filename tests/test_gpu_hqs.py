@@ -159,18 +159,17 @@ def _stack_cloud(n, colour):
     return b, z, col, m
 
 
-@pytest.mark.parametrize("mode,limit", [(pcr.PC_VIEW_HQS_PACKED, 257),
-                                        (pcr.PC_VIEW_HQS, 16_843_009)])
-def test_sum_field_limits(cuda_lib, mode, limit):
-    """At the largest count its fields hold, a pixel averages exactly; one point
-    more raises the device error flag (PC_EDEVICE at the next synchronizing
-    call), and the context keeps working."""
+def test_two_word_sum_limit(cuda_lib):
+    """At the largest count the 32-bit sums hold, a pixel averages exactly; one
+    point more raises the device error flag (PC_EDEVICE at the next
+    synchronizing call), and the context keeps working."""
     import torch
+    limit = 16_843_009
     with pcr.Context(0) as ctx:
         for n, ok in ((limit, True), (limit + 1, False), (3, True)):
             b, z, col, m = _stack_cloud(n, 0x00FFFFFF)
             cloud = ctx.upload_encoded(b, z, z, z, col)
-            v = pcr.make_view(m, 4, 4, pcr.PC_VIEW_FORCE_K(1) | mode)
+            v = pcr.make_view(m, 4, 4, pcr.PC_VIEW_FORCE_K(1) | pcr.PC_VIEW_HQS)
             [(vis, img)] = ctx.render(cloud, [v])
             torch.cuda.synchronize()
             if ok:
@@ -183,6 +182,29 @@ def test_sum_field_limits(cuda_lib, mode, limit):
                 with pytest.raises(pcr.PCError) as e:
                     ctx.stats()
                 assert e.value.status == pcr.PC_EDEVICE
+            pcr.pc_release_cloud(ctx.h, cloud)
+
+
+def test_packed_fallback_is_exact(cuda_lib):
+    """The packed sums hold 1023 points; a pixel with more is summed again by
+    the second pass, so every count gives the exact average."""
+    import torch
+    rng = np.random.default_rng(4)
+    with pcr.Context(0) as ctx:
+        for n in (1, 1023, 1024, 1027, 5000, 300_000):
+            b, z, _, m = _stack_cloud(n, 0)
+            col = rng.integers(0, 1 << 24, n, dtype=np.uint32)
+            cloud = ctx.upload_encoded(b, z, z, z, col)
+            v = pcr.make_view(m, 4, 4, pcr.PC_VIEW_FORCE_K(1) | pcr.PC_VIEW_HQS_PACKED)
+            [(vis, img)] = ctx.render(cloud, [v])
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            assert st["points_blended"] == n
+            assert st["hqs_fallback_pixels"] == (1 if n > 1023 else 0)
+            c = col.astype(np.uint64)
+            expect = (int((c & 255).sum()) // n | (int((c >> 8 & 255).sum()) // n) << 8 |
+                      (int((c >> 16 & 255).sum()) // n) << 16 | 0xFF000000)
+            assert pcr.rgba_to_numpy(img)[2 * 4 + 2] == expect
             pcr.pc_release_cloud(ctx.h, cloud)
 
 
