@@ -108,11 +108,8 @@ pc_status Ctx::ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes) {
     return PC_OK;
 }
 
-// 64-bit words of one view's region of the shading sum buffer (a whole
-// number of 16-byte words).
-static uint64_t hqs_region_words(const pc_view& v) {
-    const uint64_t w = (uint64_t)v.width * v.height * hqs_words(v.flags);
-    return (w + 1) & ~1ull;
+static uint64_t view_hqs_words(const pc_view& v) {
+    return hqs_region_words(v.flags, (uint64_t)v.width * v.height);
 }
 
 // The shading sum buffer holds the regions of every view of the largest
@@ -123,7 +120,7 @@ pc_status Ctx::ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews) {
     for (uint32_t base = 0; base < nviews; base += maxv) {
         uint64_t group = 0;
         for (uint32_t j = base; j < std::min(nviews, base + maxv); ++j)
-            group += hqs_region_words(views[j]);
+            group += view_hqs_words(views[j]);
         need = std::max(need, group);
     }
     if (need <= s.hqs_capacity) return PC_OK;
@@ -201,14 +198,14 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
             p.lod_px_periphery = pv.lod_px_periphery;
             p.vis = fbs[base + j].vis;
             p.rgba = fbs[base + j].rgba;
-            if (hqs_words(pv.flags)) {
-                if (accum_off + hqs_region_words(pv) > slot->hqs_capacity) {
+            if (hqs_mode(pv.flags)) {
+                if (accum_off + view_hqs_words(pv) > slot->hqs_capacity) {
                     fail_msg("view %u: shading sum buffer too small for its launch group",
                              base + j);
                     return PC_EINVAL;
                 }
                 p.accum = slot->hqs_accum + accum_off;
-                accum_off += hqs_region_words(pv);
+                accum_off += view_hqs_words(pv);
                 shade = true;
             }
         }
@@ -295,7 +292,7 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
         if (e != cudaSuccess) return cuda_fail(e, "graph capture");
         const uint32_t maxv = views_per_launch();
         uint64_t shaded = 0;   // the views with a colour pass change the launch layout
-        for (uint32_t v = 0; v < nviews; ++v) shaded |= (uint64_t)(hqs_words(views[v].flags) != 0);
+        for (uint32_t v = 0; v < nviews; ++v) shaded |= (uint64_t)(hqs_mode(views[v].flags) != 0);
         const uint64_t key = ((uint64_t)nviews << 8) | maxv | ((uint64_t)cl.is_lod << 40) |
                              (shaded << 41);
         cudaGraphExec_t& exec = slot->graphs[key];

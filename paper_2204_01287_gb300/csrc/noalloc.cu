@@ -64,7 +64,7 @@ extern "C" pc_status pc_render_noalloc(const pc_batch* batches, uint64_t nbatche
     if (nbatches + n_points / kNoAllocSegment + 1 > kNoAllocEntries) return PC_EINVAL;
     if (view->width == 0 || view->height == 0 || view->width > kMaxDim || view->height > kMaxDim)
         return PC_EINVAL;
-    if (hqs_words(view->flags)) return PC_ENOTSUP;   // the sum buffer would need memory
+    if (hqs_mode(view->flags)) return PC_ENOTSUP;   // the sum buffer would need memory
     const uintptr_t align = (uintptr_t)vis | (uintptr_t)rgba | (uintptr_t)w1 | (uintptr_t)w2 |
                             (uintptr_t)w3;
     if (align & 15) return PC_EINVAL;

@@ -62,14 +62,35 @@ struct ViewParams {
     unsigned long long* accum;  // high-quality shading sums (library scratch), else null
 };
 
-// Words of the high-quality shading sum buffer per pixel of a view: 2 (R | G << 32,
-// B | n << 32); packed 4 (R | G << 18 | B << 36 | n << 54, fallback flag, and the
-// two-word sums of a pixel that overflowed); 0 without shading.
 #ifdef __CUDACC__
-__host__ __device__
+#define PCR_HD __host__ __device__
+#else
+#define PCR_HD
 #endif
-inline uint32_t hqs_words(uint32_t flags) {
-    return (flags & PC_VIEW_HQS_PACKED) ? 4u : (flags & PC_VIEW_HQS) ? 2u : 0u;
+
+// High-quality shading sum buffer of one view (64-bit words), by layout:
+//   two-word: [R | G << 32, B | n << 32] per pixel (2 npix words, all cleared);
+//   packed:   P[npix] (R | G << 18 | B << 36 | n << 54), then F, a bit per pixel
+//             marking the pixels that overflowed (both cleared), then, from an even
+//             offset, two-word sums per pixel for those pixels, zeroed by the thread
+//             that sets the pixel's bit.
+// hqs_mode: 0 none, 1 two-word, 2 packed.
+PCR_HD inline uint32_t hqs_mode(uint32_t flags) {
+    return (flags & PC_VIEW_HQS_PACKED) ? 2u : (flags & PC_VIEW_HQS) ? 1u : 0u;
+}
+PCR_HD inline uint64_t hqs_flag_words(uint64_t npix) { return (npix + 63) / 64; }
+PCR_HD inline uint64_t hqs_fallback_offset(uint64_t npix) {
+    return (npix + hqs_flag_words(npix) + 1) & ~1ull;
+}
+// Words the clear pass zeroes.
+PCR_HD inline uint64_t hqs_clear_words(uint32_t flags, uint64_t npix) {
+    const uint32_t m = hqs_mode(flags);
+    return m == 1 ? 2 * npix : m == 2 ? npix + hqs_flag_words(npix) : 0;
+}
+// Words of the view's region (a whole number of 16-byte words).
+PCR_HD inline uint64_t hqs_region_words(uint32_t flags, uint64_t npix) {
+    const uint32_t m = hqs_mode(flags);
+    return m == 1 ? 2 * npix : m == 2 ? hqs_fallback_offset(npix) + 2 * npix : 0;
 }
 
 // Up to kMaxViewsPerLaunch views; lives in the kernel parameter space so that

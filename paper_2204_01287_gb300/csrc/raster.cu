@@ -56,7 +56,7 @@ __global__ void k_clear(ViewTable vt, uint32_t view_base, Scratch s) {
         // high-quality shading sums <- 0; each view's region is a whole number
         // of 16-byte words
         ulonglong2* a2 = reinterpret_cast<ulonglong2*>(vp.accum);
-        const uint64_t na = (npix * hqs_words(vp.flags) + 1) / 2;
+        const uint64_t na = (hqs_clear_words(vp.flags, npix) + 1) / 2;
         const ulonglong2 zero = make_ulonglong2(0ull, 0ull);
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na;
              i += (uint64_t)gridDim.x * blockDim.x)
@@ -647,155 +647,194 @@ __global__ void __launch_bounds__(kRasterThreads) k_rasterN(CloudView c, ViewTab
 // same pixel are summed in registers first; integer sums do not depend on the
 // order of the additions, so the result is exact.
 //
-// Sum layouts per pixel (64-bit words):
-//   two-word  [R | G << 32, B | n << 32]: two reductions per addition, no
-//             returned value; exact while n <= 16,843,009 (255 n < 2^32), which
+// Sum layouts (see hqs_region_words):
+//   two-word  [R | G << 32, B | n << 32] per pixel: two reductions per addition,
+//             no returned value; exact while n <= 16,843,009 (255 n < 2^32), which
 //             the resolve checks: a carry out of the B field needs a larger n,
 //             and n itself cannot wrap (a point is counted once).
-//   packed    [R | G << 18 | B << 36 | n << 54, fallback flag, two-word sums]:
-//             one atomicAdd per addition, exact while n <= 1023 (255 n < 2^18).
-//             The addition that takes n past 1023 sees the exact old value (the
-//             fields hold every earlier addition) and flags the pixel; a second
-//             pass then sums every point of the flagged pixels into the
-//             two-word sums, which the resolve uses there.
+//   packed    R | G << 18 | B << 36 | n << 54 per pixel: one atomicAdd per
+//             addition, exact while n <= 1023 (255 n < 2^18). The addition that
+//             takes n past 1023 sees the exact old value (the fields hold every
+//             earlier addition) and sets the pixel's overflow bit; the thread
+//             that sets it zeroes the pixel's two-word sums, and a second pass
+//             sums every point of the marked pixels there, which the resolve
+//             uses for them. The check of a returned value waits until the
+//             lane's next addition, so that the lane does not stall on it.
 
 constexpr uint32_t kHqsMaxCount = 16843009u;   // largest n with 255 n < 2^32
 constexpr uint32_t kHqsPackedMax = 1023u;      // largest n with 255 n < 2^18 and n < 2^10
 
 enum class ShadeMode { kTwoWord, kPacked, kFallback };
 
+// Where one view's sums live.
+struct ShadeBuf {
+    unsigned long long* sums;      // two-word sums, or packed words
+    unsigned long long* flags;     // packed: overflow bits
+    unsigned long long* fallback;  // packed: two-word sums of the marked pixels
+    unsigned long long* fallback_pixels;   // statistics word
+};
+
+// A packed addition whose returned value is still to be checked.
+struct PendingAdd {
+    unsigned long long old;
+    uint32_t n, pix;
+};
+
+__device__ __forceinline__ void check_packed(const ShadeBuf& sb, PendingAdd& p) {
+    if (p.n && (uint32_t)(p.old >> 54) + p.n > kHqsPackedMax) {
+        const unsigned long long bit = 1ull << (p.pix & 63u);
+        if (!(atomicOr(sb.flags + (p.pix >> 6), bit) & bit)) {
+            sb.fallback[2ull * p.pix] = 0ull;
+            sb.fallback[2ull * p.pix + 1] = 0ull;
+            atomicAdd(sb.fallback_pixels, 1ull);
+        }
+    }
+    p.n = 0;
+}
+
 template <ShadeMode MODE>
-__device__ __forceinline__ void hqs_add(unsigned long long* a, uint32_t pix, uint32_t r,
-                                        uint32_t g, uint32_t b, uint32_t n,
-                                        unsigned long long* fallback_pixels) {
-    if (MODE == ShadeMode::kTwoWord) {
-        atomicAdd(a + 2ull * pix, (unsigned long long)r | ((unsigned long long)g << 32));
-        atomicAdd(a + 2ull * pix + 1, (unsigned long long)b | ((unsigned long long)n << 32));
-    } else if (MODE == ShadeMode::kFallback) {
-        atomicAdd(a + 4ull * pix + 2, (unsigned long long)r | ((unsigned long long)g << 32));
-        atomicAdd(a + 4ull * pix + 3, (unsigned long long)b | ((unsigned long long)n << 32));
-    } else {
+__device__ __forceinline__ void hqs_add(const ShadeBuf& sb, PendingAdd& pend, uint32_t pix,
+                                        uint32_t r, uint32_t g, uint32_t b, uint32_t n) {
+    if (MODE == ShadeMode::kPacked) {
         const unsigned long long add = (unsigned long long)r | ((unsigned long long)g << 18) |
                                        ((unsigned long long)b << 36) |
                                        ((unsigned long long)n << 54);
-        const unsigned long long old = atomicAdd(a + 4ull * pix, add);
-        if ((uint32_t)(old >> 54) + n > kHqsPackedMax &&
-            atomicExch(a + 4ull * pix + 1, 1ull) == 0ull)
-            atomicAdd(fallback_pixels, 1ull);
+        const unsigned long long old = atomicAdd(sb.sums + pix, add);
+        check_packed(sb, pend);
+        pend.old = old;
+        pend.n = n;
+        pend.pix = pix;
+    } else {
+        unsigned long long* a = MODE == ShadeMode::kTwoWord ? sb.sums : sb.fallback;
+        atomicAdd(a + 2ull * pix, (unsigned long long)r | ((unsigned long long)g << 32));
+        atomicAdd(a + 2ull * pix + 1, (unsigned long long)b | ((unsigned long long)n << 32));
     }
 }
 
-template <bool PARTIAL, ShadeMode MODE>
-__device__ __forceinline__ uint32_t shade_quad(const ViewConst& vc, unsigned long long* accum,
-                                               unsigned long long* fallback_pixels,
-                                               const float (&x)[4], const float (&y)[4],
-                                               const float (&z)[4], const uint4& col,
-                                               uint32_t valid) {
-    uint32_t pix[4], w[4];
-    bool live[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float cx = clip_row4(vc.mx, x[j], y[j], z[j]);
-        const float cy = clip_row4(vc.my, x[j], y[j], z[j]);
-        const float cw = clip_row4(vc.mw, x[j], y[j], z[j]);
-        live[j] = cw > 0.0f;
-        if (PARTIAL) live[j] = live[j] && ((valid >> j) & 1u);
-        uint32_t bx = 0, by = 0;
-        if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
-        const uint32_t px = bx - 0x4B000000u, py = by - 0x4B000000u;
-        live[j] = live[j] && px < vc.width && py < vc.height;
-        w[j] = __float_as_uint(cw);
-        pix[j] = py * vc.width + px;
-    }
-    uint32_t wmin[4];
-    unsigned long long flag[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        // the depth word of the pixel's key (the upper half of the 64-bit key)
-        wmin[j] = live[j] ? reinterpret_cast<const uint32_t*>(vc.vis)[2ull * pix[j] + 1] : 0u;
-        if (MODE == ShadeMode::kFallback) flag[j] = live[j] ? accum[4ull * pix[j] + 1] : 0ull;
-    }
-    uint32_t take = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float limit = __fmul_rn(__uint_as_float(wmin[j]), 1.01f);
-        bool t = live[j] && __uint_as_float(w[j]) <= limit;
-        if (MODE == ShadeMode::kFallback) t = t && flag[j] != 0ull;
-        take |= (uint32_t)t << j;
-    }
-    if (!take) return 0;
-    const uint32_t cc[4] = {col.x, col.y, col.z, col.w};
-    uint32_t r = 0, g = 0, b = 0, n = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if (!((take >> j) & 1u)) continue;
-        r += cc[j] & 255u;
-        g += (cc[j] >> 8) & 255u;
-        b += (cc[j] >> 16) & 255u;
-        n += 1;
-        // carry the sums to the next point of the group on the same pixel
-        if (j < 3 && ((take >> (j + 1)) & 1u) && pix[j + 1] == pix[j]) continue;
-        hqs_add<MODE>(accum, pix[j], r, g, b, n, fallback_pixels);
-        r = g = b = n = 0;
-    }
-    return MODE == ShadeMode::kFallback ? 0u : (uint32_t)__popc(take);
+// Running sums of one lane: the pixel of its current run of points, that
+// pixel's depth limit fl(w_min * 1.01f) and (second pass) its fallback flag.
+struct ShadeRun {
+    uint32_t pix;
+    float limit;
+    bool flagged;
+    uint32_t r, g, b, n;
+};
+
+template <ShadeMode MODE>
+__device__ __forceinline__ void shade_flush(ShadeRun& run, const ShadeBuf& sb, PendingAdd& pend) {
+    if (run.n) hqs_add<MODE>(sb, pend, run.pix, run.r, run.g, run.b, run.n);
+    run.r = run.g = run.b = run.n = 0;
 }
 
-// Points [p0, p1) of one batch for one shaded view at precision K; the colour
-// words are loaded with the coordinate words (nearly every point of a dense
-// view falls within its pixel's window).
-template <int K, bool STREAM, ShadeMode MODE>
+// Points [p0, p1) of one batch for one shaded view at precision K. Each lane
+// walks its own contiguous share of the segment, 4 points at a time, so that
+// consecutive points (Morton order makes them neighbours) extend one run: the
+// visibility buffer is read only where a run starts, and one addition per run
+// reaches the sums. The colour words are loaded with the coordinate words
+// (nearly every point of a dense view falls within its pixel's window). The
+// loads go through L1, which keeps the other half of each 32-byte sector for
+// the lane's next group.
+template <int K, ShadeMode MODE>
 __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const ViewConst& vc,
-                                                  unsigned long long* accum,
-                                                  unsigned long long* fallback_pixels,
-                                                  const DecConst& d, uint32_t p0, uint32_t p1,
-                                                  uint32_t lane) {
+                                                  const ShadeBuf& sb, const DecConst& d,
+                                                  uint32_t p0, uint32_t p1, uint32_t lane) {
+    const uint32_t base = p0 & ~3u;
+    const uint32_t groups = (p1 - base + 3u) >> 2;
+    const uint32_t per = (groups + 31u) >> 5;
+    const uint32_t q0 = min(lane * per, groups), q1 = min(q0 + per, groups);
+    const uint32_t* vis_hi = reinterpret_cast<const uint32_t*>(vc.vis) + 1;
+    ShadeRun run;
+    run.pix = 0xFFFFFFFFu;
+    run.limit = 0.0f;
+    run.flagged = false;
+    run.r = run.g = run.b = run.n = 0;
+    PendingAdd pend;
+    pend.old = 0ull;
+    pend.n = 0;
+    pend.pix = 0;
     uint32_t n_blend = 0;
-    for (uint32_t base = p0 & ~3u; base < p1; base += 128u) {
-        const uint32_t g = base + 4u * lane;
-        if (g >= p1) continue;
-        const uint4 q1 = ld_words<STREAM>(c.w1 + g);
-        uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
-        if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
-        if (K >= 3) q3 = ld_words<STREAM>(c.w3 + g);
-        const uint4 col = ld_words<STREAM>(c.color + g);
+    for (uint32_t q = q0; q < q1; ++q) {
+        const uint32_t g = base + 4u * q;
+        const uint4 q1w = ld_words<false>(c.w1 + g);
+        uint4 q2w = make_uint4(0, 0, 0, 0), q3w = make_uint4(0, 0, 0, 0);
+        if (K >= 2) q2w = ld_words<false>(c.w2 + g);
+        if (K >= 3) q3w = ld_words<false>(c.w3 + g);
+        const uint4 col = ld_words<false>(c.color + g);
         float x[4], y[4], z[4];
-        decode_point<K>(d, q1.x, q2.x, q3.x, x[0], y[0], z[0]);
-        decode_point<K>(d, q1.y, q2.y, q3.y, x[1], y[1], z[1]);
-        decode_point<K>(d, q1.z, q2.z, q3.z, x[2], y[2], z[2]);
-        decode_point<K>(d, q1.w, q2.w, q3.w, x[3], y[3], z[3]);
-        if (g >= p0 && g + 4u <= p1) {
-            n_blend += shade_quad<false, MODE>(vc, accum, fallback_pixels, x, y, z, col, 0xFu);
-        } else {
-            uint32_t valid = 0;
+        decode_point<K>(d, q1w.x, q2w.x, q3w.x, x[0], y[0], z[0]);
+        decode_point<K>(d, q1w.y, q2w.y, q3w.y, x[1], y[1], z[1]);
+        decode_point<K>(d, q1w.z, q2w.z, q3w.z, x[2], y[2], z[2]);
+        decode_point<K>(d, q1w.w, q2w.w, q3w.w, x[3], y[3], z[3]);
+        uint32_t pix[4], w[4];
+        bool live[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
-            n_blend += shade_quad<true, MODE>(vc, accum, fallback_pixels, x, y, z, col, valid);
+        for (int j = 0; j < 4; ++j) {
+            const float cx = clip_row4(vc.mx, x[j], y[j], z[j]);
+            const float cy = clip_row4(vc.my, x[j], y[j], z[j]);
+            const float cw = clip_row4(vc.mw, x[j], y[j], z[j]);
+            live[j] = cw > 0.0f && g + j >= p0 && g + j < p1;
+            uint32_t bx = 0, by = 0;
+            if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
+            const uint32_t px = bx - 0x4B000000u, py = by - 0x4B000000u;
+            live[j] = live[j] && px < vc.width && py < vc.height;
+            w[j] = __float_as_uint(cw);
+            pix[j] = py * vc.width + px;
+        }
+        // reads for the points that start a run, issued together
+        uint32_t wmin[4];
+        bool flag[4];
+        uint32_t last = run.pix;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool start = live[j] && pix[j] != last;
+            if (live[j]) last = pix[j];
+            wmin[j] = start ? vis_hi[2ull * pix[j]] : 0u;
+            if (MODE == ShadeMode::kFallback)
+                flag[j] = start && ((sb.flags[pix[j] >> 6] >> (pix[j] & 63u)) & 1ull);
+        }
+        const uint32_t cc[4] = {col.x, col.y, col.z, col.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!live[j]) continue;
+            if (pix[j] != run.pix) {
+                shade_flush<MODE>(run, sb, pend);
+                run.pix = pix[j];
+                run.limit = __fmul_rn(__uint_as_float(wmin[j]), 1.01f);
+                if (MODE == ShadeMode::kFallback) run.flagged = flag[j];
+            }
+            bool t = __uint_as_float(w[j]) <= run.limit;
+            if (MODE == ShadeMode::kFallback) t = t && run.flagged;
+            if (t) {
+                run.r += cc[j] & 255u;
+                run.g += (cc[j] >> 8) & 255u;
+                run.b += (cc[j] >> 16) & 255u;
+                run.n += 1;
+                ++n_blend;
+            }
         }
     }
-    return n_blend;
+    shade_flush<MODE>(run, sb, pend);
+    if (MODE == ShadeMode::kPacked) check_packed(sb, pend);
+    return MODE == ShadeMode::kFallback ? 0u : n_blend;
 }
 
-template <bool STREAM, ShadeMode MODE>
+template <ShadeMode MODE>
 __device__ __forceinline__ uint32_t shade_segment_k(const CloudView& c, const ViewConst& vc,
-                                                    unsigned long long* accum,
-                                                    unsigned long long* fallback_pixels,
-                                                    const pc_batch& bt, int k, uint32_t p0,
-                                                    uint32_t p1, uint32_t lane) {
+                                                    const ShadeBuf& sb, const pc_batch& bt, int k,
+                                                    uint32_t p0, uint32_t p1, uint32_t lane) {
     const DecConst d = make_dec_const(bt, k);
-    if (k == 1) return shade_segment<1, STREAM, MODE>(c, vc, accum, fallback_pixels, d, p0, p1, lane);
-    if (k == 2) return shade_segment<2, STREAM, MODE>(c, vc, accum, fallback_pixels, d, p0, p1, lane);
-    return shade_segment<3, STREAM, MODE>(c, vc, accum, fallback_pixels, d, p0, p1, lane);
+    if (k == 1) return shade_segment<1, MODE>(c, vc, sb, d, p0, p1, lane);
+    if (k == 2) return shade_segment<2, MODE>(c, vc, sb, d, p0, p1, lane);
+    return shade_segment<3, MODE>(c, vc, sb, d, p0, p1, lane);
 }
 
 // Persistent warps take draw-list segments (a counter of their own); each
-// segment is walked once per shaded view that did not cull its batch. With one
-// shaded view per launch the loads stream past L1, as in the depth pass.
+// segment is walked once per shaded view that did not cull its batch.
 // FALLBACK: the second pass for packed views, which returns at once unless
 // one of its views flagged a pixel.
 // (No __launch_bounds__: with it ptxas held this kernel to 32 registers and
 // spilled.)
-template <bool STREAM, bool FALLBACK>
+template <bool FALLBACK>
 __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s,
                         uint32_t shade_mask) {
     __shared__ uint32_t sh_blend[kMaxViewsPerLaunch];
@@ -829,17 +868,23 @@ __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s
             const uint32_t v = __ffs(mm) - 1;
             const ViewConst vc = make_view_const(vt.v[v]);
             const int k = (int)((e.kcodes >> (2 * v)) & 3u);
-            unsigned long long* fbp = &s.stats[(uint64_t)(view_base + v) * S_COUNT + S_FALLBACK];
+            const ViewParams& vp = vt.v[v];
+            const uint64_t npix = (uint64_t)vp.width * vp.height;
+            ShadeBuf sb;
+            sb.sums = vp.accum;
+            sb.flags = vp.accum + npix;
+            sb.fallback = vp.accum + hqs_fallback_offset(npix);
+            sb.fallback_pixels = &s.stats[(uint64_t)(view_base + v) * S_COUNT + S_FALLBACK];
             uint32_t n;
             if (FALLBACK)
-                n = shade_segment_k<STREAM, ShadeMode::kFallback>(
-                    c, vc, vt.v[v].accum, fbp, bt, k, p0, p0 + e.seg_count, lane);
-            else if (vt.v[v].flags & PC_VIEW_HQS_PACKED)
-                n = shade_segment_k<STREAM, ShadeMode::kPacked>(
-                    c, vc, vt.v[v].accum, fbp, bt, k, p0, p0 + e.seg_count, lane);
+                n = shade_segment_k<ShadeMode::kFallback>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
+                                                          lane);
+            else if (vp.flags & PC_VIEW_HQS_PACKED)
+                n = shade_segment_k<ShadeMode::kPacked>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
+                                                        lane);
             else
-                n = shade_segment_k<STREAM, ShadeMode::kTwoWord>(
-                    c, vc, vt.v[v].accum, fbp, bt, k, p0, p0 + e.seg_count, lane);
+                n = shade_segment_k<ShadeMode::kTwoWord>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
+                                                         lane);
             const uint32_t t = __reduce_add_sync(FULL, n);
             if (lane == 0 && t) atomicAdd(&sh_blend[v], t);
         }
@@ -860,7 +905,7 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
     if (!vp.rgba) return;
     const uint64_t npix = (uint64_t)vp.width * vp.height;
     const bool dilate = (vp.flags & PC_VIEW_DILATE) != 0;
-    const uint32_t words = vp.accum ? hqs_words(vp.flags) : 0u;
+    const uint32_t mode = vp.accum ? hqs_mode(vp.flags) : 0u;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (uint64_t)gridDim.x * blockDim.x) {
         unsigned long long key = vp.vis[p];
@@ -883,28 +928,26 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
                 }
         }
         uint32_t out = 0u;
-        if (words && key != ~0ull) {
+        if (mode && key != ~0ull) {
             // Sec. 3.6: per-channel average of the sums, rounded down
-            const ulonglong2* a2 = reinterpret_cast<const ulonglong2*>(vp.accum);
             uint32_t r, g, b, n;
-            ulonglong2 two;   // two-word sums
-            bool use_two = words == 2;
-            if (words == 2) {
-                two = a2[at];
-            } else {
-                const ulonglong2 head = a2[2 * at];   // packed sums, fallback flag
-                use_two = head.y != 0ull;
-                if (use_two) two = a2[2 * at + 1];
-                r = (uint32_t)(head.x & 0x3FFFFu);
-                g = (uint32_t)((head.x >> 18) & 0x3FFFFu);
-                b = (uint32_t)((head.x >> 36) & 0x3FFFFu);
-                n = (uint32_t)(head.x >> 54);
+            const ulonglong2* two = reinterpret_cast<const ulonglong2*>(vp.accum);   // two-word sums
+            bool use_two = mode == 1;
+            if (mode == 2) {
+                use_two = (vp.accum[npix + (at >> 6)] >> (at & 63)) & 1ull;
+                two = reinterpret_cast<const ulonglong2*>(vp.accum + hqs_fallback_offset(npix));
+                const unsigned long long a = vp.accum[at];
+                r = (uint32_t)(a & 0x3FFFFu);
+                g = (uint32_t)((a >> 18) & 0x3FFFFu);
+                b = (uint32_t)((a >> 36) & 0x3FFFFu);
+                n = (uint32_t)(a >> 54);
             }
             if (use_two) {
-                r = (uint32_t)two.x;
-                g = (uint32_t)(two.x >> 32);
-                b = (uint32_t)two.y;
-                n = (uint32_t)(two.y >> 32);
+                const ulonglong2 t = two[at];
+                r = (uint32_t)t.x;
+                g = (uint32_t)(t.x >> 32);
+                b = (uint32_t)t.y;
+                n = (uint32_t)(t.y >> 32);
                 if (n > kHqsMaxCount) raise_error(s, E_HQS_OVERFLOW, (uint32_t)at);
             }
             if (n) out = (r / n) | ((g / n) << 8) | ((b / n) << 16) | 0xFF000000u;
@@ -978,13 +1021,13 @@ cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view
     return cudaGetLastError();
 }
 
-template <bool STREAM, bool FALLBACK>
+template <bool FALLBACK>
 static cudaError_t launch_shade_kernel(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                                        Scratch s, int threads, uint32_t mask, cudaStream_t st) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<STREAM, FALLBACK>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<FALLBACK>, threads, 0);
     const int blocks = num_sms() * (nb > 0 ? nb : 1);
-    k_shade<STREAM, FALLBACK><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
+    k_shade<FALLBACK><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
     return cudaGetLastError();
 }
 
@@ -992,7 +1035,7 @@ cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_
                          RasterShape shape, cudaStream_t st, int* launched) {
     uint32_t mask = 0, packed = 0;
     for (uint32_t v = 0; v < vt.n; ++v) {
-        if (!vt.v[v].accum || !hqs_words(vt.v[v].flags)) continue;
+        if (!vt.v[v].accum || !hqs_mode(vt.v[v].flags)) continue;
         mask |= 1u << v;
         if (vt.v[v].flags & PC_VIEW_HQS_PACKED) packed |= 1u << v;
     }
@@ -1000,14 +1043,10 @@ cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_
     if (!mask) return cudaSuccess;
     int threads = shape.threads_per_block > 0 ? shape.threads_per_block : kRasterThreads;
     threads = threads > kRasterThreads ? kRasterThreads : (threads < 32 ? 32 : threads & ~31);
-    const bool stream = (mask & (mask - 1)) == 0;
-    cudaError_t e = stream ? launch_shade_kernel<true, false>(c, vt, view_base, s, threads, mask, st)
-                           : launch_shade_kernel<false, false>(c, vt, view_base, s, threads, mask, st);
+    cudaError_t e = launch_shade_kernel<false>(c, vt, view_base, s, threads, mask, st);
     *launched = 1;
     if (e != cudaSuccess || !packed) return e;
-    const bool stream2 = (packed & (packed - 1)) == 0;
-    e = stream2 ? launch_shade_kernel<true, true>(c, vt, view_base, s, threads, packed, st)
-                : launch_shade_kernel<false, true>(c, vt, view_base, s, threads, packed, st);
+    e = launch_shade_kernel<true>(c, vt, view_base, s, threads, packed, st);
     *launched = 2;
     return e;
 }
