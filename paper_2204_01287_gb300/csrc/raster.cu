@@ -333,6 +333,47 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Packed binary32 pairs (sm_100 f32x2 instructions), used where two independent
+// operations of the same kind sit side by side. Each half is rounded exactly as
+// the scalar instruction would round it. A packed multiply never feeds a packed
+// add: ptxas contracts that pair into a packed fused multiply-add, which changes
+// the bits. Every add after a packed multiply is a scalar __fadd_rn.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(f2_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2_t f2_fma_rn(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+__device__ __forceinline__ f2_t f2_fma_rd(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // ---- k_raster -------------------------------------------------------------------
 //
 // Every lane takes an aligned group of 4 consecutive points (one 16-byte load
@@ -411,13 +452,22 @@ __device__ __forceinline__ float q_to_float(uint32_t q) {
 }
 
 // Decoded position (Sec. 3.3): x = min + float(X) * cell per axis, binary32.
+// float(X) and the products of x and y are formed as one packed pair each.
 template <int K>
 __device__ __forceinline__ void decode_point(const DecConst& d, uint32_t a, uint32_t b, uint32_t c,
                                              float& x, float& y, float& z) {
     uint32_t qx, qy, qz;
     decode_q<K>(a, b, c, qx, qy, qz);
-    x = __fadd_rn(d.mn[0], __fmul_rn(q_to_float<K>(qx), d.cell[0]));
-    y = __fadd_rn(d.mn[1], __fmul_rn(q_to_float<K>(qy), d.cell[1]));
+    f2_t fxy;
+    if (K <= 2)
+        fxy = f2_sub(f2_pack(__uint_as_float(0x4B000000u | qx), __uint_as_float(0x4B000000u | qy)),
+                     f2_pack(8388608.0f, 8388608.0f));
+    else
+        fxy = f2_pack(__uint2float_rn(qx), __uint2float_rn(qy));
+    float sx, sy;
+    f2_unpack(f2_mul(fxy, f2_pack(d.cell[0], d.cell[1])), sx, sy);
+    x = __fadd_rn(d.mn[0], sx);
+    y = __fadd_rn(d.mn[1], sy);
     z = __fadd_rn(d.mn[2], __fmul_rn(q_to_float<K>(qz), d.cell[2]));
 }
 
@@ -441,25 +491,26 @@ __device__ __forceinline__ uint32_t exact_floor_bits(float c, float w, float W) 
 // with room for the roundings of both sides whenever |q'| <= 1.01, so
 // fl_down(u- * W + 2^23) <= floor bits <= fl_down(u+ * W + 2^23); when the two
 // ends agree they are the floor bits. Points with |q'| > 1.01 lie outside the
-// viewport either way. Returns false (use the exact path) when they differ.
-__device__ __forceinline__ bool fast_floor_bits(float c, float r, float W, uint32_t& bits) {
-    const float q = __fmul_rn(c, r);
-    const float ulo = __fmaf_rn(q, 0.5f, 0.5f - 0x1.0p-21f);
-    const float uhi = __fmaf_rn(q, 0.5f, 0.5f + 0x1.0p-21f);
-    const uint32_t blo = __float_as_uint(__fmaf_rd(ulo, W, 8388608.0f));
-    const uint32_t bhi = __float_as_uint(__fmaf_rd(uhi, W, 8388608.0f));
-    bits = blo;
-    return blo == bhi;
-}
+// viewport either way. The x and y axes run as packed pairs.
 
 // Floor bits of both axes of one point with w > 0.
 __device__ __forceinline__ void pixel_bits(float cx, float cy, float cw, float W, float H,
                                            uint32_t& bx, uint32_t& by) {
     float r = rcp_approx(cw);
     r = __fmaf_rn(r, __fmaf_rn(-cw, r, 1.0f), r);
-    const bool ok = fast_floor_bits(cx, r, W, bx) & fast_floor_bits(cy, r, H, by) &
-                    (cw >= 0x1.0p-100f) & (cw <= 0x1.0p100f);
-    if (!ok) {
+    const f2_t half = f2_pack(0.5f, 0.5f);
+    const f2_t magic = f2_pack(8388608.0f, 8388608.0f);
+    const f2_t wh = f2_pack(W, H);
+    const f2_t q = f2_mul(f2_pack(cx, cy), f2_pack(r, r));
+    const f2_t ulo = f2_fma_rn(q, half, f2_pack(0.5f - 0x1.0p-21f, 0.5f - 0x1.0p-21f));
+    const f2_t uhi = f2_fma_rn(q, half, f2_pack(0.5f + 0x1.0p-21f, 0.5f + 0x1.0p-21f));
+    const f2_t blo = f2_fma_rd(ulo, wh, magic);
+    const f2_t bhi = f2_fma_rd(uhi, wh, magic);
+    const bool ok = (blo == bhi) & (cw >= 0x1.0p-100f) & (cw <= 0x1.0p100f);
+    if (ok) {
+        bx = (uint32_t)blo;
+        by = (uint32_t)(blo >> 32);
+    } else {
         bx = exact_floor_bits(cx, cw, W);
         by = exact_floor_bits(cy, cw, H);
     }
