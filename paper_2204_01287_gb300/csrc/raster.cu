@@ -356,6 +356,12 @@ __device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
     return r;
 }
 
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 __device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
     f2_t r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -406,6 +412,23 @@ __device__ __forceinline__ ViewConst make_view_const(const ViewParams& v) {
     c.vis = reinterpret_cast<unsigned long long*>(v.vis);
     c.early = !(v.flags & PC_VIEW_NO_EARLY_DEPTH);
     return c;
+}
+
+// The clip coordinates of one point (Listing 1), each row as
+// ((m[r] x + m[r+4] y) + m[r+8] z) + m[r+12]. The x and y rows share their
+// products' operands, so their products are packed pairs; the sums are scalar
+// adds, except the last one, whose operands are sums.
+__device__ __forceinline__ void clip_xyw(const ViewConst& vc, float x, float y, float z, float& cx,
+                                         float& cy, float& cw) {
+    float a0, a1, b0, b1, c0, c1, w0, w1;
+    f2_unpack(f2_mul(f2_pack(vc.mx[0], vc.my[0]), f2_pack(x, x)), a0, a1);
+    f2_unpack(f2_mul(f2_pack(vc.mx[1], vc.my[1]), f2_pack(y, y)), b0, b1);
+    f2_unpack(f2_mul(f2_pack(vc.mx[2], vc.my[2]), f2_pack(z, z)), c0, c1);
+    f2_unpack(f2_mul(f2_pack(vc.mw[0], vc.mw[1]), f2_pack(x, y)), w0, w1);
+    const float sx = __fadd_rn(__fadd_rn(a0, b0), c0);
+    const float sy = __fadd_rn(__fadd_rn(a1, b1), c1);
+    f2_unpack(f2_add(f2_pack(sx, sy), f2_pack(vc.mx[3], vc.my[3])), cx, cy);
+    cw = __fadd_rn(__fadd_rn(__fadd_rn(w0, w1), __fmul_rn(vc.mw[2], z)), vc.mw[3]);
 }
 
 // Per-batch decode constants at precision k.
@@ -533,9 +556,8 @@ __device__ __forceinline__ uint32_t raster_quad(const ViewConst& vc, const float
     bool live[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float cx = clip_row4(vc.mx, x[j], y[j], z[j]);
-        const float cy = clip_row4(vc.my, x[j], y[j], z[j]);
-        const float cw = clip_row4(vc.mw, x[j], y[j], z[j]);
+        float cx, cy, cw;
+        clip_xyw(vc, x[j], y[j], z[j], cx, cy, cw);
         live[j] = cw > 0.0f;
         if (PARTIAL) live[j] = live[j] && ((valid >> j) & 1u);
         uint32_t bx = 0, by = 0;
@@ -820,9 +842,8 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
         bool live[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float cx = clip_row4(vc.mx, x[j], y[j], z[j]);
-            const float cy = clip_row4(vc.my, x[j], y[j], z[j]);
-            const float cw = clip_row4(vc.mw, x[j], y[j], z[j]);
+            float cx, cy, cw;
+            clip_xyw(vc, x[j], y[j], z[j], cx, cy, cw);
             live[j] = cw > 0.0f && g + j >= p0 && g + j < p1;
             uint32_t bx = 0, by = 0;
             if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
