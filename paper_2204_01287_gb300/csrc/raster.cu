@@ -541,18 +541,19 @@ __device__ __forceinline__ void pixel_bits(float cx, float cy, float cw, float W
 
 // Listing 1 for the four points of a group: project, test, then the
 // early-depth reads of all four, then atomicMin of (bits(w) << 32 | index)
-// where the key is smaller. A stale early-depth read is larger than or equal
-// to the current value, so it can only cause an unnecessary atomic, never a
-// missed one. A key sent to a pixel is carried to the next point of the group
-// when it lands on the same pixel, so consecutive points (Morton order makes
-// them neighbours) do not repeat the atomic. PARTIAL groups carry a validity
+// where the point may be closer. The early-depth read takes only the depth
+// half of the pixel's key, and a point goes on to the atomic when its depth
+// bits are not above it: a tie in depth issues an atomic that atomicMin then
+// settles by index. A stale read is larger than or equal to the current value,
+// so it can only cause an unnecessary atomic, never a missed one. After an
+// atomic, the next point of the group on the same pixel needs one only if it
+// is strictly closer (its index is larger). PARTIAL groups carry a validity
 // mask. Returns the number of atomicMin issued.
 template <bool PARTIAL>
 __device__ __forceinline__ uint32_t raster_quad(const ViewConst& vc, const float (&x)[4],
                                                 const float (&y)[4], const float (&z)[4],
                                                 uint32_t idx0, uint32_t valid) {
-    unsigned long long key[4];
-    uint32_t pix[4];
+    uint32_t w[4], pix[4];
     bool live[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -564,19 +565,22 @@ __device__ __forceinline__ uint32_t raster_quad(const ViewConst& vc, const float
         if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
         const uint32_t px = bx - 0x4B000000u, py = by - 0x4B000000u;
         live[j] = live[j] && px < vc.width && py < vc.height;
-        key[j] = ((unsigned long long)__float_as_uint(cw) << 32) | (unsigned long long)(idx0 + j);
+        w[j] = __float_as_uint(cw);
         pix[j] = py * vc.width + px;
     }
-    unsigned long long old[4];
+    // depth halves of the pixels' keys (0xFFFFFFFF: no read, always try)
+    const uint32_t* vis_hi = reinterpret_cast<const uint32_t*>(vc.vis) + 1;
+    uint32_t lim[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) old[j] = (live[j] && vc.early) ? vc.vis[pix[j]] : ~0ull;
+    for (int j = 0; j < 4; ++j) lim[j] = (live[j] && vc.early) ? vis_hi[2ull * pix[j]] : 0xFFFFFFFFu;
     uint32_t n_atom = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (live[j] && key[j] < old[j]) {
-            atomicMin(vc.vis + pix[j], key[j]);
+        if (live[j] && w[j] <= lim[j]) {
+            atomicMin(vc.vis + pix[j], ((unsigned long long)w[j] << 32) | (idx0 + j));
             ++n_atom;
-            if (j < 3 && pix[j + 1] == pix[j] && key[j] < old[j + 1]) old[j + 1] = key[j];
+            // w > 0 here, so w - 1 does not wrap
+            if (j < 3 && pix[j + 1] == pix[j]) lim[j + 1] = min(lim[j + 1], w[j] - 1u);
         }
     }
     return n_atom;
