@@ -516,9 +516,11 @@ __device__ __forceinline__ uint32_t exact_floor_bits(float c, float w, float W) 
 // ends agree they are the floor bits. Points with |q'| > 1.01 lie outside the
 // viewport either way. The x and y axes run as packed pairs.
 
-// Floor bits of both axes of one point with w > 0.
-__device__ __forceinline__ void pixel_bits(float cx, float cy, float cw, float W, float H,
-                                           uint32_t& bx, uint32_t& by) {
+// Floor bits of both axes of one point by the certified fast path; false when
+// the two ends of the bracket differ or w is outside [2^-100, 2^100] (then the
+// exact path decides). Any w may be passed: nothing here can fault.
+__device__ __forceinline__ bool pixel_bits_fast(float cx, float cy, float cw, float W, float H,
+                                                uint32_t& bx, uint32_t& by) {
     float r = rcp_approx(cw);
     r = __fmaf_rn(r, __fmaf_rn(-cw, r, 1.0f), r);
     const f2_t half = f2_pack(0.5f, 0.5f);
@@ -529,11 +531,15 @@ __device__ __forceinline__ void pixel_bits(float cx, float cy, float cw, float W
     const f2_t uhi = f2_fma_rn(q, half, f2_pack(0.5f + 0x1.0p-21f, 0.5f + 0x1.0p-21f));
     const f2_t blo = f2_fma_rd(ulo, wh, magic);
     const f2_t bhi = f2_fma_rd(uhi, wh, magic);
-    const bool ok = (blo == bhi) & (cw >= 0x1.0p-100f) & (cw <= 0x1.0p100f);
-    if (ok) {
-        bx = (uint32_t)blo;
-        by = (uint32_t)(blo >> 32);
-    } else {
+    bx = (uint32_t)blo;
+    by = (uint32_t)(blo >> 32);
+    return (blo == bhi) & (cw >= 0x1.0p-100f) & (cw <= 0x1.0p100f);
+}
+
+// Floor bits of both axes of one point with w > 0.
+__device__ __forceinline__ void pixel_bits(float cx, float cy, float cw, float W, float H,
+                                           uint32_t& bx, uint32_t& by) {
+    if (!pixel_bits_fast(cx, cy, cw, W, H, bx, by)) {
         bx = exact_floor_bits(cx, cw, W);
         by = exact_floor_bits(cy, cw, H);
     }
@@ -553,19 +559,31 @@ template <bool PARTIAL>
 __device__ __forceinline__ uint32_t raster_quad(const ViewConst& vc, const float (&x)[4],
                                                 const float (&y)[4], const float (&z)[4],
                                                 uint32_t idx0, uint32_t valid) {
-    uint32_t w[4], pix[4];
+    uint32_t w[4], pix[4], bx[4], by[4];
+    float cx[4], cy[4], cw[4];
     bool live[4];
+    uint32_t slow = 0;   // live points whose bracket did not settle the pixel
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float cx, cy, cw;
-        clip_xyw(vc, x[j], y[j], z[j], cx, cy, cw);
-        live[j] = cw > 0.0f;
+        clip_xyw(vc, x[j], y[j], z[j], cx[j], cy[j], cw[j]);
+        live[j] = cw[j] > 0.0f;
         if (PARTIAL) live[j] = live[j] && ((valid >> j) & 1u);
-        uint32_t bx = 0, by = 0;
-        if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
-        const uint32_t px = bx - 0x4B000000u, py = by - 0x4B000000u;
+        const bool ok = pixel_bits_fast(cx[j], cy[j], cw[j], vc.W, vc.H, bx[j], by[j]);
+        slow |= (uint32_t)(live[j] && !ok) << j;
+    }
+    if (slow) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((slow >> j) & 1u) {
+                bx[j] = exact_floor_bits(cx[j], cw[j], vc.W);
+                by[j] = exact_floor_bits(cy[j], cw[j], vc.H);
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t px = bx[j] - 0x4B000000u, py = by[j] - 0x4B000000u;
         live[j] = live[j] && px < vc.width && py < vc.height;
-        w[j] = __float_as_uint(cw);
+        w[j] = __float_as_uint(cw[j]);
         pix[j] = py * vc.width + px;
     }
     // depth halves of the pixels' keys (0xFFFFFFFF: no read, always try)
