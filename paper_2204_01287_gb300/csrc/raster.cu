@@ -591,6 +591,10 @@ __device__ __forceinline__ uint32_t raster_quad(const ViewConst& vc, const float
     uint32_t lim[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) lim[j] = (live[j] && vc.early) ? vis_hi[2ull * pix[j]] : 0xFFFFFFFFu;
+    uint32_t need = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) need |= (uint32_t)(live[j] && w[j] <= lim[j]) << j;
+    if (!need) return 0;   // the common case: every point is behind its pixel's depth
     uint32_t n_atom = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
