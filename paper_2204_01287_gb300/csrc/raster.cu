@@ -588,9 +588,16 @@ __device__ __forceinline__ uint32_t raster_quad(const ViewConst& vc, const float
     }
     // depth halves of the pixels' keys (0xFFFFFFFF: no read, always try)
     const uint32_t* vis_hi = reinterpret_cast<const uint32_t*>(vc.vis) + 1;
+    // a point on the pixel of the group's previous point reuses that read
     uint32_t lim[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) lim[j] = (live[j] && vc.early) ? vis_hi[2ull * pix[j]] : 0xFFFFFFFFu;
+    for (int j = 0; j < 4; ++j) {
+        const bool same = j > 0 && live[j - 1] && pix[j] == pix[j - 1];
+        lim[j] = (live[j] && vc.early && !same) ? vis_hi[2ull * pix[j]] : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int j = 1; j < 4; ++j)
+        if (live[j - 1] && pix[j] == pix[j - 1]) lim[j] = lim[j - 1];
     uint32_t need = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) need |= (uint32_t)(live[j] && w[j] <= lim[j]) << j;
@@ -625,30 +632,53 @@ __device__ __forceinline__ uint4 ld_words(const uint32_t* p) {
 // Points [p0, p1) of one batch for one view at precision K. The loop over
 // groups of 4 is warp-uniform; STREAM loads bypass L1 (single view), the
 // multi-view kernel keeps the words in cache for the next view.
+// One lane's group of 4 points at g: load, decode, raster.
+template <int K, bool STREAM, bool PARTIAL>
+__device__ __forceinline__ uint32_t raster_group(const CloudView& c, const ViewConst& vc,
+                                                 const DecConst& d, uint32_t g, uint32_t valid) {
+    const uint4 q1 = ld_words<STREAM>(c.w1 + g);
+    uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
+    if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
+    if (K >= 3) q3 = ld_words<STREAM>(c.w3 + g);
+    float x[4], y[4], z[4];
+    decode_point<K>(d, q1.x, q2.x, q3.x, x[0], y[0], z[0]);
+    decode_point<K>(d, q1.y, q2.y, q3.y, x[1], y[1], z[1]);
+    decode_point<K>(d, q1.z, q2.z, q3.z, x[2], y[2], z[2]);
+    decode_point<K>(d, q1.w, q2.w, q3.w, x[3], y[3], z[3]);
+    return raster_quad<PARTIAL>(vc, x, y, z, g, valid);
+}
+
+// Points [p0, p1) of one batch for one view at precision K, 128 points per
+// warp step. Steps that lie wholly inside the range (all of them but the last
+// for batches that start on a multiple of 128, as batches of 10,240 do) need
+// no bounds checks; the first step of an unaligned range and the last step
+// carry a validity mask. STREAM loads bypass L1 (single view), the multi-view
+// kernel keeps the words in cache for the next view.
 template <int K, bool STREAM>
 __device__ __forceinline__ uint32_t segment(const CloudView& c, const ViewConst& vc,
                                             const DecConst& d, uint32_t p0, uint32_t p1,
                                             uint32_t lane) {
     uint32_t n_atom = 0;
-    for (uint32_t base = p0 & ~3u; base < p1; base += 128u) {
+    uint32_t base = p0 & ~3u;
+    if (base != p0 && base < p1) {
         const uint32_t g = base + 4u * lane;
-        if (g >= p1) continue;
-        const uint4 q1 = ld_words<STREAM>(c.w1 + g);
-        uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
-        if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
-        if (K >= 3) q3 = ld_words<STREAM>(c.w3 + g);
-        float x[4], y[4], z[4];
-        decode_point<K>(d, q1.x, q2.x, q3.x, x[0], y[0], z[0]);
-        decode_point<K>(d, q1.y, q2.y, q3.y, x[1], y[1], z[1]);
-        decode_point<K>(d, q1.z, q2.z, q3.z, x[2], y[2], z[2]);
-        decode_point<K>(d, q1.w, q2.w, q3.w, x[3], y[3], z[3]);
-        if (g >= p0 && g + 4u <= p1) {
-            n_atom += raster_quad<false>(vc, x, y, z, g, 0xFu);
-        } else {
+        if (g < p1) {
             uint32_t valid = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
-            n_atom += raster_quad<true>(vc, x, y, z, g, valid);
+            n_atom += raster_group<K, STREAM, true>(c, vc, d, g, valid);
+        }
+        base += 128u;
+    }
+    for (; base + 128u <= p1; base += 128u)
+        n_atom += raster_group<K, STREAM, false>(c, vc, d, base + 4u * lane, 0xFu);
+    if (base < p1) {
+        const uint32_t g = base + 4u * lane;
+        if (g < p1) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j < p1) << j;
+            n_atom += raster_group<K, STREAM, true>(c, vc, d, g, valid);
         }
     }
     return n_atom;
