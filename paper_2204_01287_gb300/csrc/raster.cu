@@ -536,15 +536,6 @@ __device__ __forceinline__ bool pixel_bits_fast(float cx, float cy, float cw, fl
     return (blo == bhi) & (cw >= 0x1.0p-100f) & (cw <= 0x1.0p100f);
 }
 
-// Floor bits of both axes of one point with w > 0.
-__device__ __forceinline__ void pixel_bits(float cx, float cy, float cw, float W, float H,
-                                           uint32_t& bx, uint32_t& by) {
-    if (!pixel_bits_fast(cx, cy, cw, W, H, bx, by)) {
-        bx = exact_floor_bits(cx, cw, W);
-        by = exact_floor_bits(cy, cw, H);
-    }
-}
-
 // Listing 1 for the four points of a group: project, test, then the
 // early-depth reads of all four, then atomicMin of (bits(w) << 32 | index)
 // where the point may be closer. The early-depth read takes only the depth
@@ -894,18 +885,30 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
         decode_point<K>(d, q1w.y, q2w.y, q3w.y, x[1], y[1], z[1]);
         decode_point<K>(d, q1w.z, q2w.z, q3w.z, x[2], y[2], z[2]);
         decode_point<K>(d, q1w.w, q2w.w, q3w.w, x[3], y[3], z[3]);
-        uint32_t pix[4], w[4];
+        uint32_t pix[4], w[4], bx[4], by[4];
+        float cx[4], cy[4], cw[4];
         bool live[4];
+        uint32_t slow = 0;   // live points whose bracket did not settle the pixel
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float cx, cy, cw;
-            clip_xyw(vc, x[j], y[j], z[j], cx, cy, cw);
-            live[j] = cw > 0.0f && g + j >= p0 && g + j < p1;
-            uint32_t bx = 0, by = 0;
-            if (live[j]) pixel_bits(cx, cy, cw, vc.W, vc.H, bx, by);
-            const uint32_t px = bx - 0x4B000000u, py = by - 0x4B000000u;
+            clip_xyw(vc, x[j], y[j], z[j], cx[j], cy[j], cw[j]);
+            live[j] = cw[j] > 0.0f && g + j >= p0 && g + j < p1;
+            const bool ok = pixel_bits_fast(cx[j], cy[j], cw[j], vc.W, vc.H, bx[j], by[j]);
+            slow |= (uint32_t)(live[j] && !ok) << j;
+        }
+        if (slow) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((slow >> j) & 1u) {
+                    bx[j] = exact_floor_bits(cx[j], cw[j], vc.W);
+                    by[j] = exact_floor_bits(cy[j], cw[j], vc.H);
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t px = bx[j] - 0x4B000000u, py = by[j] - 0x4B000000u;
             live[j] = live[j] && px < vc.width && py < vc.height;
-            w[j] = __float_as_uint(cw);
+            w[j] = __float_as_uint(cw[j]);
             pix[j] = py * vc.width + px;
         }
         // reads for the points that start a run, issued together
