@@ -169,7 +169,7 @@ __device__ __forceinline__ double row_mag(const double r[4], const double lo[3],
     return s;
 }
 
-__device__ bool cull_batch(const pc_batch& b, const ViewParams& v) {
+__device__ bool cull_batch_exact(const pc_batch& b, const ViewParams& v) {
     const double g = 6.0 * 0x1.0p-24;
     const double e1 = 1.0 + 0x1.0p-10;
     double lo[3], hi[3];
@@ -203,6 +203,86 @@ __device__ bool cull_batch(const pc_batch& b, const ViewParams& v) {
     if (__dadd_rn(row_max(sp, lo, hi), my) < 0.0) return true;
     if (__dsub_rn(row_min(sm, lo, hi), my) > 0.0) return true;
     return false;
+}
+
+// The same five tests in binary32 first. Each test value t approximates the
+// exact value R of its expression within about 10 * 2^-24 of the magnitude M
+// of its terms, and the binary64 value within about 10 * 2^-53 M, so when
+// |t| > 2^-16 M both have the sign of R and the decision equals the binary64
+// one. Inside that band, or when a magnitude is not finite or below 2^-90
+// (where products could lose bits to underflow), the binary64 code decides.
+// Returns 1 culled, 0 not culled, -1 undecided.
+__device__ __forceinline__ float row_max32(const float r[4], const float lo[3], const float hi[3]) {
+    float s = r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s = __fadd_rn(s, fmaxf(__fmul_rn(r[a], lo[a]), __fmul_rn(r[a], hi[a])));
+    return s;
+}
+__device__ __forceinline__ float row_min32(const float r[4], const float lo[3], const float hi[3]) {
+    float s = r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s = __fadd_rn(s, fminf(__fmul_rn(r[a], lo[a]), __fmul_rn(r[a], hi[a])));
+    return s;
+}
+__device__ __forceinline__ float row_mag32(const float r[4], const float lo[3], const float hi[3]) {
+    float s = fabsf(r[3]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        s = __fadd_rn(s, __fmul_rn(fabsf(r[a]), fmaxf(fabsf(lo[a]), fabsf(hi[a]))));
+    return s;
+}
+
+__device__ __forceinline__ int cull_batch_fast(const pc_batch& b, const ViewParams& v) {
+    const float g = 6.0f * 0x1.0p-24f;
+    const float e1 = 1.0f + 0x1.0p-10f;
+    const float band = 0x1.0p-16f;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = b.min[a];
+        hi[a] = __fadd_rn(b.min[a], b.size[a]);
+    }
+    const float* m = v.m;
+    const float X[4] = {m[0], m[4], m[8], m[12]};
+    const float Y[4] = {m[1], m[5], m[9], m[13]};
+    const float Wr[4] = {m[3], m[7], m[11], m[15]};
+    const float bx = row_mag32(X, lo, hi), by = row_mag32(Y, lo, hi), bw = row_mag32(Wr, lo, hi);
+    const float mag_x = __fadd_rn(bx, __fmul_rn(e1, bw)), mag_y = __fadd_rn(by, __fmul_rn(e1, bw));
+    if (!(bw <= 0x1.0p100f) || !(mag_x <= 0x1.0p100f) || !(mag_y <= 0x1.0p100f)) return -1;
+    if (!(bw >= 0x1.0p-90f) || !(mag_x >= 0x1.0p-90f) || !(mag_y >= 0x1.0p-90f)) return -1;
+    // each test: culled when t < 0 (t <= 0 for the w plane), decided when |t| > band M
+    bool undecided = false, culled = false;
+    auto test = [&](float t, float mag) {
+        const float lim = __fmul_rn(band, mag);
+        if (t < -lim) culled = true;
+        else if (!(t > lim)) undecided = true;
+    };
+    test(__fadd_rn(row_max32(Wr, lo, hi), __fmul_rn(g, bw)), bw);
+    float sp[4], sm[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        sp[a] = __fadd_rn(X[a], __fmul_rn(e1, Wr[a]));
+        sm[a] = __fsub_rn(X[a], __fmul_rn(e1, Wr[a]));
+    }
+    const float mx = __fmul_rn(g, mag_x);
+    test(__fadd_rn(row_max32(sp, lo, hi), mx), mag_x);
+    test(-__fsub_rn(row_min32(sm, lo, hi), mx), mag_x);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        sp[a] = __fadd_rn(Y[a], __fmul_rn(e1, Wr[a]));
+        sm[a] = __fsub_rn(Y[a], __fmul_rn(e1, Wr[a]));
+    }
+    const float my = __fmul_rn(g, mag_y);
+    test(__fadd_rn(row_max32(sp, lo, hi), my), mag_y);
+    test(-__fsub_rn(row_min32(sm, lo, hi), my), mag_y);
+    // a test decided as culling settles it; otherwise every test must be decided
+    if (culled) return 1;
+    return undecided ? -1 : 0;
+}
+
+__device__ __forceinline__ bool cull_batch(const pc_batch& b, const ViewParams& v) {
+    const int r = cull_batch_fast(b, v);
+    return r < 0 ? cull_batch_exact(b, v) : r == 1;
 }
 
 constexpr int kCullThreads = 128;
