@@ -287,6 +287,20 @@ __device__ __forceinline__ bool cull_batch(const pc_batch& b, const ViewParams& 
 
 constexpr int kCullThreads = 128;
 
+// Sum of a 64-bit value over the 32 lanes of a warp (butterfly on 32-bit
+// halves with the carry).
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+    uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const uint32_t ol = __shfl_xor_sync(FULL, lo, d), oh = __shfl_xor_sync(FULL, hi, d);
+        const uint32_t nl = lo + ol;
+        hi = hi + oh + (nl < lo ? 1u : 0u);
+        lo = nl;
+    }
+    return ((unsigned long long)hi << 32) | lo;
+}
+
 // Sec. 3.5: a node passes a view when it is in the frustum and, unless it is
 // the root, its projected extent reaches the view's threshold (a corner with
 // w <= 0 counts as large). lod_sel[n] gets one bit per view of the launch.
@@ -360,19 +374,37 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
             const int k = select_k(bt, vp, vt.threshold_px);
             mask |= 1u << v;
             kcodes |= (uint64_t)k << (2 * v);
-            atomicAdd(&sh_stats[v * S_COUNT + S_BATCHES], 1ull);
-            atomicAdd(&sh_stats[v * S_COUNT + S_BK1 + (k - 1)], 1ull);
-            atomicAdd(&sh_stats[v * S_COUNT + S_PK1 + (k - 1)], (unsigned long long)count);
         }
-        if (mask) {
-            nseg = (count + vt.seg_points - 1) / vt.seg_points;
-            uint32_t kl = 0;
-            for (uint32_t v = 0; v < vt.n; ++v) kl = max(kl, (uint32_t)((kcodes >> (2 * v)) & 3u));
-            atomicAdd(&sh_words, (unsigned long long)kl * count);
+        if (mask) nseg = (count + vt.seg_points - 1) / vt.seg_points;
+    }
+    const uint32_t lane = threadIdx.x & 31;
+    // statistics, summed over the warp first: one shared-memory addition per
+    // warp and counter (64-bit shared atomics contend badly lane by lane)
+    uint32_t kl = 0;
+    for (uint32_t v = 0; v < vt.n; ++v) {
+        const bool drawn = (mask >> v) & 1u;
+        if (!__any_sync(FULL, drawn)) continue;
+        const uint32_t k = (uint32_t)((kcodes >> (2 * v)) & 3u);
+        if (drawn) kl = max(kl, k);
+        uint32_t nb = 0;
+#pragma unroll
+        for (uint32_t kk = 1; kk <= 3; ++kk) {
+            const bool sel = drawn && k == kk;
+            const uint32_t n = __popc(__ballot_sync(FULL, sel));
+            const unsigned long long pts = warp_sum_u64(sel ? count : 0u);
+            nb += n;
+            if (lane == 0 && n) {
+                atomicAdd(&sh_stats[v * S_COUNT + S_BK1 + (kk - 1)], (unsigned long long)n);
+                atomicAdd(&sh_stats[v * S_COUNT + S_PK1 + (kk - 1)], pts);
+            }
         }
+        if (lane == 0) atomicAdd(&sh_stats[v * S_COUNT + S_BATCHES], (unsigned long long)nb);
+    }
+    {
+        const unsigned long long words = warp_sum_u64((unsigned long long)kl * (mask ? count : 0u));
+        if (lane == 0 && words) atomicAdd(&sh_words, words);
     }
     // warp-aggregated append of nseg entries
-    const uint32_t lane = threadIdx.x & 31;
     uint32_t incl = nseg;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
