@@ -435,9 +435,16 @@ def lod_bench(args, pcr, torch, ctx, params):
             ctx.render(cloud, [v], fbs)
         e1.record()
         torch.cuda.synchronize()
+        pcr.pc_timing_begin(ctx.h)
+        for v in views[::10]:
+            ctx.render(cloud, [v], fbs)
+        t = pcr.pc_timing_end(ctx.h)
+        f = max(1, t.frames)
         out[name] = {"ms_per_frame": e0.elapsed_time(e1) / len(views),
                      "batches_rendered_avg": nodes / len(views[::10]),
-                     "points_processed_avg": pts / len(views[::10])}
+                     "points_processed_avg": pts / len(views[::10]),
+                     "passes_ms": {"clear": t.ms_clear / f, "select_and_cull": t.ms_cull / f,
+                                   "raster": t.ms_raster / f, "resolve": t.ms_resolve / f}}
     out["speedup_vs_brute_force"] = out["brute_force"]["ms_per_frame"] / out["lod"]["ms_per_frame"]
     # LOD with high-quality shading (Sec. 3.5 with Sec. 3.6), both sum layouts
     for hname, flag in (("lod_hqs_two_word", pcr.PC_VIEW_HQS),

@@ -163,9 +163,17 @@ RasterShape Ctx::shape_for(uint32_t nviews) {
     return r;
 }
 
-uint32_t Ctx::seg_points_for(uint32_t nviews) const {
+// Points per draw-list segment: the tuned size, made smaller (down to
+// kMinSegmentPoints, in multiples of 128) when the cloud is too small to give
+// every resident raster warp about four segments. LOD frames draw a small part
+// of their cloud, so they take the smallest size.
+uint32_t Ctx::seg_points_for(uint32_t nviews, const Cloud& cl, const RasterShape& shape) const {
     const Tune& t = tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
-    return t.seg_points ? t.seg_points : kSegmentPoints;
+    const uint32_t seg = t.seg_points ? t.seg_points : kSegmentPoints;
+    if (cl.is_lod) return kMinSegmentPoints;
+    const uint64_t warps = std::max<uint64_t>(1, (uint64_t)shape.blocks * shape.threads_per_block / 32);
+    const uint64_t fit = (cl.n_points / (4 * warps)) & ~127ull;
+    return (uint32_t)std::max<uint64_t>(kMinSegmentPoints, std::min<uint64_t>(seg, fit));
 }
 
 uint32_t Ctx::views_per_launch() const {
@@ -186,7 +194,8 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
         std::memset(&vt, 0, sizeof vt);
         vt.n = std::min(maxv, nviews - base);
         vt.threshold_px = cfg.precision_px;
-        vt.seg_points = seg_points_for(vt.n);
+        const RasterShape shape = shape_for(vt.n);
+        vt.seg_points = seg_points_for(vt.n, cl, shape);
         for (uint32_t j = 0; j < vt.n; ++j) {
             const pc_view& pv = views[base + j];
             ViewParams& p = vt.v[j];
@@ -228,12 +237,12 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
         e = launch_cull(cv, vt, base, slot->scratch, st);
         if (e != cudaSuccess) return cuda_fail(e, "cull launch");
         if (fe) cudaEventRecord(fe->ev[2], st);
-        e = launch_raster(cv, vt, base, slot->scratch, shape_for(vt.n), st);
+        e = launch_raster(cv, vt, base, slot->scratch, shape, st);
         if (e != cudaSuccess) return cuda_fail(e, "raster launch");
         if (fe) cudaEventRecord(fe->ev[3], st);
         if (shade) {
             int nk = 0;
-            e = launch_shade(cv, vt, base, slot->scratch, shape_for(vt.n), st, &nk);
+            e = launch_shade(cv, vt, base, slot->scratch, shape, st, &nk);
             if (e != cudaSuccess) return cuda_fail(e, "shading launch");
             launches += nk;
         }

@@ -97,7 +97,7 @@ struct Ctx {
     pc_status ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes);
     pc_status ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews);
     RasterShape shape_for(uint32_t nviews);
-    uint32_t seg_points_for(uint32_t nviews) const;
+    uint32_t seg_points_for(uint32_t nviews, const Cloud& cl, const RasterShape& shape) const;
     uint32_t views_per_launch() const;
     pc_status launch_frame(const Cloud& cl, const pc_view* views, uint32_t nviews,
                            const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);

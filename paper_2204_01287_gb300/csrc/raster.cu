@@ -1149,6 +1149,42 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
     const uint64_t npix = (uint64_t)vp.width * vp.height;
     const bool dilate = (vp.flags & PC_VIEW_DILATE) != 0;
     const uint32_t mode = vp.accum ? hqs_mode(vp.flags) : 0u;
+    if (!dilate && !mode) {
+        // plain resolve, 4 pixels per thread: two 16-byte key loads, four
+        // independent colour gathers, one 16-byte store (vis and rgba are
+        // 16-byte aligned); the last npix % 4 pixels one by one
+        const uint64_t n4 = npix / 4;
+        const ulonglong2* vis2 = reinterpret_cast<const ulonglong2*>(vp.vis);
+        uint4* out4 = reinterpret_cast<uint4*>(vp.rgba);
+        for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
+             q += (uint64_t)gridDim.x * blockDim.x) {
+            const ulonglong2 a = vis2[2 * q], b = vis2[2 * q + 1];
+            const unsigned long long key[4] = {a.x, a.y, b.x, b.y};
+            uint32_t col[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                col[j] = 0u;
+                if (key[j] != ~0ull) {
+                    const uint32_t idx = (uint32_t)key[j];
+                    if (idx < c.n_points) col[j] = __ldg(c.color + idx);
+                    else raise_error(s, E_INDEX_RANGE, idx);
+                }
+            }
+            out4[q] = make_uint4(col[0], col[1], col[2], col[3]);
+        }
+        for (uint64_t p = 4 * n4 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+             p += (uint64_t)gridDim.x * blockDim.x) {
+            const unsigned long long key = vp.vis[p];
+            uint32_t out = 0u;
+            if (key != ~0ull) {
+                const uint32_t idx = (uint32_t)key;
+                if (idx < c.n_points) out = c.color[idx];
+                else raise_error(s, E_INDEX_RANGE, idx);
+            }
+            vp.rgba[p] = out;
+        }
+        return;
+    }
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (uint64_t)gridDim.x * blockDim.x) {
         unsigned long long key = vp.vis[p];
