@@ -343,19 +343,25 @@ typedef struct {
     pc_status status;         /* PC_OK or the failure of this request */
     uint32_t  nviews;
     uint32_t* const* rgba;    /* host images, one per view, owned by the context
-                                 until pc_release_ticket */
+                                 until pc_release_ticket; NULL for requests with
+                                 caller-owned framebuffers */
     const uint32_t* widths;
     const uint32_t* heights;
     double    t_submit_ms, t_start_ms, t_done_ms;   /* steady clock, ms since ctx creation */
 } pc_result;
 
-/* Queue a request: nviews (1..32) views of a resident cloud. The library owns
- * the framebuffers (admitted when serve_pool_bytes has room and a view slot
- * is free) and returns host RGBA images through pc_poll. Requests that arrive
- * while others run join the next launch group of the same cloud. Returns
- * PC_EBUSY when the request can never fit the pool. */
+/* Queue a request: nviews (1..32) views of a resident cloud. Requests that
+ * arrive while others run join the next launch group of the same cloud.
+ * fbs == NULL: the library owns the framebuffers (admitted when
+ * serve_pool_bytes has room and a view slot is free) and returns host RGBA
+ * images through pc_poll; PC_EBUSY when the request can never fit the pool
+ * or the pinned image memory is full.
+ * fbs != NULL: nviews caller-owned device framebuffers (as for pc_render,
+ * 16-byte aligned, vis required); nothing is admitted or copied to the host,
+ * the images are in fbs once pc_poll reports the request done, and the caller
+ * must not use them before. */
 pc_status pc_submit(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
-                    pc_ticket* out);
+                    const pc_framebuffer* fbs, pc_ticket* out);
 
 /* Wait up to timeout_ms (0 = just test, < 0 = no limit) for a request.
  * PC_ETIMEDOUT if it has not finished; on PC_OK *out describes the result. */

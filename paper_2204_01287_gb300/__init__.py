@@ -146,7 +146,7 @@ SIGNATURES = [
     ("pc_set_views_per_launch", _i32, [_vp, _u32]),
     ("pc_timing_begin", _i32, [_vp]),
     ("pc_timing_end", _i32, [_vp, _P(pc_timing)]),
-    ("pc_submit", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_u64)]),
+    ("pc_submit", _i32, [_vp, _u64, _P(pc_view), _u32, _P(pc_framebuffer), _P(_u64)]),
     ("pc_poll", _i32, [_vp, _u64, _i32, _P(pc_result)]),
     ("pc_release_ticket", _i32, [_vp, _u64]),
 ]
@@ -355,10 +355,17 @@ def pc_timing_end(ctx: int) -> pc_timing:
     return t
 
 
-def pc_submit(ctx: int, cloud: int, views) -> int:
+def pc_submit(ctx: int, cloud: int, views, fbs=None) -> int:
+    """fbs: None (library-owned framebuffers, host images from pc_poll) or a
+    list of (vis, rgba) device pointers, one per view."""
     va = _views_arr(views)
+    fa = None
+    if fbs is not None:
+        fa = (pc_framebuffer * len(views))()
+        for i, (vis, rgba) in enumerate(fbs):
+            fa[i].vis, fa[i].rgba = vis, rgba
     out = ctypes.c_uint64()
-    _check(ctx, lib().pc_submit(ctx, cloud, va, len(views), ctypes.byref(out)))
+    _check(ctx, lib().pc_submit(ctx, cloud, va, len(views), fa, ctypes.byref(out)))
     return out.value
 
 
@@ -371,7 +378,7 @@ def pc_poll(ctx: int, ticket: int, timeout_ms: int = -1):
         return rc, None
     _check(ctx, rc)
     imgs = []
-    for v in range(r.nviews):
+    for v in range(r.nviews if r.rgba else 0):
         n = r.widths[v] * r.heights[v]
         imgs.append(np.ctypeslib.as_array(r.rgba[v], shape=(n,)).copy())
     return rc, {"status": r.status, "images": imgs, "t_submit_ms": r.t_submit_ms,

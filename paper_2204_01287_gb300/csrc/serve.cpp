@@ -75,6 +75,7 @@ struct Request {
     std::shared_ptr<Cloud> cloud;
     std::vector<pc_view> views;
     std::vector<uint64_t> dev_off;    // per view: vis at dev_off, rgba after it
+    std::vector<pc_framebuffer> user_fb;   // caller-owned framebuffers (else empty)
     std::vector<uint32_t*> host;      // per view pinned image
     std::vector<uint32_t> widths, heights;
     uint64_t dev_bytes = 0, dev_base = 0;
@@ -145,8 +146,12 @@ void launch_group(ServeState& s, Lane& lane, std::vector<Request*>& group) {
             views.push_back(r->views[v]);
             const uint64_t npix = (uint64_t)r->views[v].width * r->views[v].height;
             pc_framebuffer fb;
-            fb.vis = reinterpret_cast<uint64_t*>(s.dev_base + r->dev_off[v]);
-            fb.rgba = reinterpret_cast<uint32_t*>(s.dev_base + r->dev_off[v] + round_up(npix * 8));
+            if (!r->user_fb.empty()) {
+                fb = r->user_fb[v];
+            } else {
+                fb.vis = reinterpret_cast<uint64_t*>(s.dev_base + r->dev_off[v]);
+                fb.rgba = reinterpret_cast<uint32_t*>(s.dev_base + r->dev_off[v] + round_up(npix * 8));
+            }
             fbs.push_back(fb);
         }
     }
@@ -157,6 +162,7 @@ void launch_group(ServeState& s, Lane& lane, std::vector<Request*>& group) {
     for (Request* r : group) {
         for (size_t v = 0; v < r->views.size(); ++v, ++k) {
             if (rc != PC_OK) break;
+            if (!r->user_fb.empty()) continue;   // the images stay in the caller's framebuffers
             const uint64_t npix = (uint64_t)r->views[v].width * r->views[v].height;
             cudaError_t e = cudaMemcpyAsync(r->host[v], fbs[k].rgba, npix * 4,
                                             cudaMemcpyDeviceToHost, lane.stream);
@@ -204,19 +210,21 @@ bool next_group(ServeState& s, std::vector<Request*>& group) {
             ++it;
             continue;
         }
-        uint64_t off = 0;
-        if (!s.dev.alloc(r->dev_bytes, off)) {
-            if (aged) break;
-            ++it;
-            continue;
-        }
-        r->dev_base = off;
-        r->has_dev = true;
-        uint64_t o = off;
-        for (size_t v = 0; v < r->views.size(); ++v) {
-            r->dev_off[v] = o;
-            const uint64_t npix = (uint64_t)r->views[v].width * r->views[v].height;
-            o += round_up(npix * 8) + round_up(npix * 4);
+        if (r->user_fb.empty()) {
+            uint64_t off = 0;
+            if (!s.dev.alloc(r->dev_bytes, off)) {
+                if (aged) break;
+                ++it;
+                continue;
+            }
+            r->dev_base = off;
+            r->has_dev = true;
+            uint64_t o = off;
+            for (size_t v = 0; v < r->views.size(); ++v) {
+                r->dev_off[v] = o;
+                const uint64_t npix = (uint64_t)r->views[v].width * r->views[v].height;
+                o += round_up(npix * 8) + round_up(npix * 4);
+            }
         }
         group.push_back(r);
         nviews += (uint32_t)r->views.size();
@@ -315,7 +323,7 @@ using namespace pcr;
 extern "C" {
 
 pc_status pc_submit(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nviews,
-                    pc_ticket* out) {
+                    const pc_framebuffer* fbs, pc_ticket* out) {
     if (!h || !views || !out || nviews == 0 || nviews > kMaxViewsPerRequest) return PC_EINVAL;
     Ctx* ctx = reinterpret_cast<Ctx*>(h);
     *out = 0;
@@ -339,13 +347,28 @@ pc_status pc_submit(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nv
         const pc_view& pv = views[v];
         if (pv.width == 0 || pv.height == 0 || pv.width > kMaxDim || pv.height > kMaxDim)
             return PC_EINVAL;
+        if (fbs && (!fbs[v].vis || ((uintptr_t)fbs[v].vis & 15) || ((uintptr_t)fbs[v].rgba & 15))) {
+            ctx->fail_msg("view %u: framebuffer missing or not 16-byte aligned", v);
+            return PC_EINVAL;
+        }
         const uint64_t npix = (uint64_t)pv.width * pv.height;
-        r->dev_bytes += round_up(npix * 8) + round_up(npix * 4);
-        r->host_bytes += round_up(npix * 4);
         r->widths.push_back(pv.width);
         r->heights.push_back(pv.height);
+        if (fbs) continue;
+        r->dev_bytes += round_up(npix * 8) + round_up(npix * 4);
+        r->host_bytes += round_up(npix * 4);
     }
+    if (fbs) r->user_fb.assign(fbs, fbs + nviews);
     std::lock_guard<std::mutex> g(s.mu);
+    if (fbs) {
+        r->id = ++s.next;
+        r->t_submit = ctx->now_ms();
+        *out = r->id;
+        s.queue.push_back(r.get());
+        s.reqs[r->id] = std::move(r);
+        s.cv_work.notify_all();
+        return PC_OK;
+    }
     if (r->dev_bytes > s.dev.size || r->host_bytes > s.host.size) {
         ctx->fail_msg("request needs %llu device bytes, pool holds %llu",
                       (unsigned long long)r->dev_bytes, (unsigned long long)s.dev.size);
@@ -391,7 +414,7 @@ pc_status pc_poll(pc_ctx* h, pc_ticket ticket, int32_t timeout_ms, pc_result* ou
     std::memset(out, 0, sizeof *out);
     out->status = r->status;
     out->nviews = (uint32_t)r->views.size();
-    out->rgba = r->host.data();
+    out->rgba = r->user_fb.empty() ? r->host.data() : nullptr;
     out->widths = r->widths.data();
     out->heights = r->heights.data();
     out->t_submit_ms = r->t_submit;

@@ -219,3 +219,41 @@ def test_graph_replay_keeps_bits(world):
                 assert np.array_equal(pcr.rgba_to_numpy(img), alone(ctx, c1, v))
     finally:
         g.close()
+
+
+def test_caller_owned_framebuffers(world):
+    """Requests that bring their own device framebuffers: nothing is admitted
+    or copied to the host, and the images in the caller's buffers equal the
+    same views rendered alone; they batch with library-owned requests."""
+    import torch
+    ctx, (c1, p1), (c2, p2) = world
+    reqs = _requests(c1, p1, c2, p2, 12, seed=7)
+    owned = []
+    tickets = []
+    for i, (cloud, views) in enumerate(reqs):
+        if i % 2 == 0:
+            fbs = ctx.framebuffers(views)
+            owned.append(fbs)
+            tickets.append(pcr.pc_submit(ctx.h, cloud, views,
+                                         [(a.data_ptr(), b.data_ptr()) for a, b in fbs]))
+        else:
+            owned.append(None)
+            tickets.append(pcr.pc_submit(ctx.h, cloud, views))
+    for i, t in enumerate(tickets):
+        rc, res = pcr.pc_poll(ctx.h, t, 60_000)
+        assert rc == pcr.PC_OK and res["status"] == pcr.PC_OK
+        cloud, views = reqs[i]
+        if owned[i] is not None:
+            assert res["images"] == []
+            got = [pcr.rgba_to_numpy(img) for _, img in owned[i]]
+        else:
+            got = res["images"]
+        for v, img in zip(views, got):
+            assert np.array_equal(img, alone(ctx, cloud, v))
+        pcr.pc_release_ticket(ctx.h, t)
+    # misaligned caller framebuffers are refused
+    v = reqs[0][1][:1]
+    buf = torch.empty(v[0].width * v[0].height + 2, dtype=torch.int64, device="cuda")
+    with pytest.raises(pcr.PCError) as e:
+        pcr.pc_submit(ctx.h, reqs[0][0], v, [(buf.data_ptr() + 8, 0)])
+    assert e.value.status == pcr.PC_EINVAL
