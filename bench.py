@@ -502,6 +502,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def replica_throughput(ms_local, points_per_frame, steps, world):
+    """(ms, Gpoints/s) of `world` replicas that each rendered the same `steps`
+    frames of `points_per_frame` points: the slowest rank's time (a max over
+    the process group when world > 1) and the whole job's points over it."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, points_per_frame * steps * world / (ms / 1e3) / 1e9
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -569,13 +583,8 @@ def main():
         torch.distributed.barrier()
     clocks = sampler.stop()
     timing = pcr.pc_timing_end(ctx.h)
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = replica_throughput(e0.elapsed_time(e1), points_per_frame, args.steps, world)
     ms_per_frame = ms / args.steps
-    value = points_per_frame * args.steps * world / (ms / 1e3) / 1e9
 
     raster_ms = timing.ms_raster / max(1, timing.frames)
     peak, peak_kind = peaks()
