@@ -140,6 +140,7 @@ def lib():
             L.or_render_hqs.argtypes = [vp, u64, vp, vp, vp, vp, VP, vp, vp]
             L.or_lod_render_hqs.argtypes = [vp, vp, u64, vp, vp, vp, vp, VP, f32, f32, vp, vp]
             L.or_hqs_resolve_dilated.argtypes = [vp, u32, u32, vp, vp]
+            L.or_verify_encoding.argtypes = [vp, vp, u64, u32, vp, u64, vp, vp, vp, vp, vp, i32, vp]
             _lib = L
     return _lib
 
@@ -413,3 +414,18 @@ def hqs_resolve_dilated(vis: np.ndarray, width: int, height: int, hqs: np.ndarra
     out = np.empty(width * height, np.uint32)
     lib().or_hqs_resolve_dilated(_p(vis), width, height, _p(hqs), _p(out))
     return out
+
+
+def verify_encoding(xyz, rgba, batch_size, batches, w1, w2, w3, color, perm, threads=0):
+    """(code, where): 0 when the arrays are the unique encoding of (xyz, rgba)
+    defined by Sec. 3.1, Eq. 1 and Listing 2 (see or_verify_encoding)."""
+    import os
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    arrs = [np.ascontiguousarray(a, np.uint32) for a in (w1, w2, w3, color, perm)]
+    b = np.ascontiguousarray(batches, BATCH_DTYPE)
+    where = np.zeros(1, np.uint64)
+    code = lib().or_verify_encoding(_p(xyz), _p(rgba) if rgba is not None else None, len(xyz),
+                                    int(batch_size), _p(b), len(b), *(_p(a) for a in arrs),
+                                    int(threads or os.cpu_count() or 1), _p(where))
+    return int(code), int(where[0])

@@ -835,3 +835,160 @@ void or_hqs_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height
             out[(uint64_t)py * width + px] = best == OR_EMPTY ? 0u : hqs[at];
         }
 }
+
+/* ---- Sec. 3.1 at full size: checking an encoding against the definition ---- */
+
+typedef struct {
+    const float* xyz;
+    const uint32_t* rgba;
+    uint64_t n;
+    uint32_t batch_size;
+    const or_batch* batches;
+    uint64_t nbatches;
+    const uint32_t *w1, *w2, *w3, *color, *perm;
+    double cmin[3], csize[3];
+    uint64_t lo, hi;         /* range of sorted positions (pass 1) or batches (pass 2) */
+    float bmin[3], bmax[3];  /* pass 0: box of xyz[lo, hi) */
+    int code;
+    uint64_t where;
+} verify_job;
+
+static void* verify_box(void* a) {
+    verify_job* j = (verify_job*)a;
+    for (int c = 0; c < 3; ++c) j->bmin[c] = j->bmax[c] = j->xyz[3 * j->lo + c];
+    for (uint64_t i = j->lo; i < j->hi; ++i)
+        for (int c = 0; c < 3; ++c) {
+            float v = j->xyz[3 * i + c];
+            if (v < j->bmin[c]) j->bmin[c] = v;
+            if (v > j->bmax[c]) j->bmax[c] = v;
+        }
+    return NULL;
+}
+
+/* pass 1: perm sorts the Morton codes stably. Its entries are below n, and
+ * strictly increasing (code, index) pairs make them distinct, so it is a
+ * permutation. */
+static void* verify_order(void* a) {
+    verify_job* j = (verify_job*)a;
+    uint64_t prev_code = 0;
+    uint32_t prev_idx = 0;
+    if (j->lo > 0) {
+        prev_idx = j->perm[j->lo - 1];
+        if ((uint64_t)prev_idx < j->n) prev_code = or_morton_code(&j->xyz[3 * (uint64_t)prev_idx], j->cmin, j->csize);
+    }
+    for (uint64_t i = j->lo; i < j->hi; ++i) {
+        uint32_t idx = j->perm[i];
+        if ((uint64_t)idx >= j->n) { j->code = 2; j->where = i; return NULL; }
+        uint64_t code = or_morton_code(&j->xyz[3 * (uint64_t)idx], j->cmin, j->csize);
+        if (i > 0 && !(prev_code < code || (prev_code == code && prev_idx < idx))) {
+            j->code = 3; j->where = i; return NULL;
+        }
+        prev_code = code;
+        prev_idx = idx;
+    }
+    return NULL;
+}
+
+/* pass 2: batch headers, boxes, Eq. 1 words (Listing 2) and colours */
+static void* verify_batches(void* a) {
+    verify_job* j = (verify_job*)a;
+    for (uint64_t b = j->lo; b < j->hi; ++b) {
+        const or_batch* B = &j->batches[b];
+        uint64_t first = b * j->batch_size;
+        uint64_t end = first + j->batch_size < j->n ? first + j->batch_size : j->n;
+        if (B->first != first || B->count != end - first) { j->code = 1; j->where = b; return NULL; }
+        float bmin[3], bmax[3];
+        for (int c = 0; c < 3; ++c) bmin[c] = bmax[c] = j->xyz[3 * (uint64_t)j->perm[first] + c];
+        for (uint64_t i = first; i < end; ++i)
+            for (int c = 0; c < 3; ++c) {
+                float v = j->xyz[3 * (uint64_t)j->perm[i] + c];
+                if (v < bmin[c]) bmin[c] = v;
+                if (v > bmax[c]) bmax[c] = v;
+            }
+        for (int c = 0; c < 3; ++c) {
+            float size = bmax[c] - bmin[c];
+            if (memcmp(&B->min[c], &bmin[c], 4) != 0 || memcmp(&B->size[c], &size, 4) != 0) {
+                j->code = 4; j->where = b; return NULL;
+            }
+        }
+        for (uint64_t i = first; i < end; ++i) {
+            const float* p = &j->xyz[3 * (uint64_t)j->perm[i]];
+            uint32_t w[3];
+            or_split_words(or_quantize30(p[0], B->min[0], B->size[0]),
+                           or_quantize30(p[1], B->min[1], B->size[1]),
+                           or_quantize30(p[2], B->min[2], B->size[2]), w);
+            if (w[0] != j->w1[i] || w[1] != j->w2[i] || w[2] != j->w3[i]) {
+                j->code = 5; j->where = i; return NULL;
+            }
+            uint32_t col = j->rgba ? j->rgba[j->perm[i]] : 0u;
+            if (col != j->color[i]) { j->code = 6; j->where = i; return NULL; }
+        }
+    }
+    return NULL;
+}
+
+static void run_jobs(verify_job* jobs, int threads, void* (*fn)(void*)) {
+    pthread_t* tid = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    int* ok = (int*)calloc((size_t)threads, sizeof(int));
+    for (int t = 0; t < threads; ++t) {
+        ok[t] = pthread_create(&tid[t], NULL, fn, &jobs[t]) == 0;
+        if (!ok[t]) fn(&jobs[t]);
+    }
+    for (int t = 0; t < threads; ++t)
+        if (ok[t]) pthread_join(tid[t], NULL);
+    free(tid);
+    free(ok);
+}
+
+int or_verify_encoding(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
+                       const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                       const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
+                       const uint32_t* perm, int threads, uint64_t* where) {
+    *where = 0;
+    if (batch_size == 0 || n > 0xFFFFFFFFull || nbatches != or_num_batches(n, batch_size)) return 1;
+    if (n == 0) return 0;
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    verify_job* jobs = (verify_job*)calloc((size_t)threads, sizeof(verify_job));
+    if (!jobs) return -2;
+    for (int t = 0; t < threads; ++t) {
+        verify_job* j = &jobs[t];
+        j->xyz = xyz; j->rgba = rgba; j->n = n; j->batch_size = batch_size;
+        j->batches = batches; j->nbatches = nbatches;
+        j->w1 = w1; j->w2 = w2; j->w3 = w3; j->color = color; j->perm = perm;
+        j->lo = n * (uint64_t)t / (uint64_t)threads;
+        j->hi = n * (uint64_t)(t + 1) / (uint64_t)threads;
+    }
+    /* the cloud box, as the encoder takes it */
+    run_jobs(jobs, threads, verify_box);
+    float lo[3], hi[3];
+    int have = 0;
+    for (int t = 0; t < threads; ++t) {
+        if (jobs[t].hi <= jobs[t].lo) continue;
+        for (int c = 0; c < 3; ++c) {
+            if (!have || jobs[t].bmin[c] < lo[c]) lo[c] = jobs[t].bmin[c];
+            if (!have || jobs[t].bmax[c] > hi[c]) hi[c] = jobs[t].bmax[c];
+        }
+        have = 1;
+    }
+    for (int t = 0; t < threads; ++t)
+        for (int c = 0; c < 3; ++c) {
+            jobs[t].cmin[c] = (double)lo[c];
+            jobs[t].csize[c] = (double)hi[c] - (double)lo[c];
+        }
+    int code = 0;
+    run_jobs(jobs, threads, verify_order);
+    for (int t = 0; t < threads && !code; ++t)
+        if (jobs[t].code) { code = jobs[t].code; *where = jobs[t].where; }
+    if (!code) {
+        for (int t = 0; t < threads; ++t) {
+            jobs[t].lo = nbatches * (uint64_t)t / (uint64_t)threads;
+            jobs[t].hi = nbatches * (uint64_t)(t + 1) / (uint64_t)threads;
+        }
+        run_jobs(jobs, threads, verify_batches);
+        for (int t = 0; t < threads && !code; ++t)
+            if (jobs[t].code) { code = jobs[t].code; *where = jobs[t].where; }
+    }
+    free(jobs);
+    return code;
+}

@@ -205,6 +205,20 @@ void or_lod_render_hqs(const or_batch* nodes, const uint32_t* parent, uint64_t n
 void or_hqs_resolve_dilated(const uint64_t* vis, uint32_t width, uint32_t height,
                             const uint32_t* hqs, uint32_t* out);
 
+/* Check an encoding of n points against Sec. 3.1, Eq. 1 and Listing 2, in
+ * O(n) on `threads` threads: perm must be a permutation that sorts the Morton
+ * codes (over the cloud box) with ties in input order, batches must be the
+ * consecutive runs of batch_size sorted points with their binary32 boxes,
+ * and w1/w2/w3/color the split Eq. 1 coordinates and colours. The encoding
+ * is unique, so one that passes equals or_encode's. Returns 0, or the first
+ * failure found: 1 batch count/header, 2 not a permutation, 3 order, 4 box,
+ * 5 words, 6 colour, with its index (sorted position or batch) in *where;
+ * -2 when out of memory. */
+int or_verify_encoding(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t batch_size,
+                       const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                       const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
+                       const uint32_t* perm, int threads, uint64_t* where);
+
 /* Sec. 3.3 visibility buffer: out[p] = colour of the winning point, 0 where
  * no point landed. */
 void or_resolve(const uint64_t* vis, uint64_t npixels, const uint32_t* color,

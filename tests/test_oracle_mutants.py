@@ -64,8 +64,20 @@ HQS_MUTANTS = [
      "best == OR_EMPTY ? 0u : hqs[(uint64_t)py * width + px];"),
 ]
 
+# the full-size encoding checker, checked by tests/test_oracle_verify.py
+VERIFY_MUTANTS = [
+    ("verify_no_order", "if (i > 0 && !(prev_code < code || (prev_code == code && prev_idx < idx))) {",
+     "if (0) {"),
+    ("verify_no_tiebreak", "(prev_code == code && prev_idx < idx)", "(prev_code == code)"),
+    ("verify_no_box", "if (memcmp(&B->min[c], &bmin[c], 4) != 0 || memcmp(&B->size[c], &size, 4) != 0) {",
+     "if (0) {"),
+    ("verify_no_range", "if ((uint64_t)idx >= j->n) { j->code = 2; j->where = i; return NULL; }",
+     "if (0) { j->code = 2; j->where = i; return NULL; }"),
+]
+
 CASES = ([m + ("test_oracle_pins.py",) for m in MUTANTS] +
-         [m + ("test_oracle_hqs.py",) for m in HQS_MUTANTS])
+         [m + ("test_oracle_hqs.py",) for m in HQS_MUTANTS] +
+         [m + ("test_oracle_verify.py",) for m in VERIFY_MUTANTS])
 
 
 @pytest.mark.parametrize("name,old,new,pins", CASES, ids=[m[0] for m in CASES])
