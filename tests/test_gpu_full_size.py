@@ -1,0 +1,62 @@
+"""The bench's workload at full size.
+
+The cloud is 2,000,000,000 terrain+building points over 40 km. It is encoded by
+the library's host encoder and rendered in the bench's launch configuration
+(autotuned raster shape): the 1920x1080 overview frame, and the stereo pair of
+2016x2240 per eye in one launch.
+
+The oracle cannot sort 2B points in a test's time, but it checks the library's
+encoding against Sec. 3.1, Eq. 1 and Listing 2 in O(n). That encoding is unique,
+so an encoding that passes is the oracle's. The oracle then renders the same
+frames itself on all host cores, and every pixel of every view must match.
+About 75 GB of host memory and two minutes.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2204_01287_gb300 as pcr
+import pcsynth as S
+
+pytestmark = pytest.mark.gpu
+
+N = 2_000_000_000
+BATCH = 10240
+
+
+def test_full_size_frames_bit_exact(cuda_lib):
+    import torch
+    params = S.terrain_params(40000.0, 0.2, 20000)
+    xyz = np.empty((N, 3), np.float32)
+    rgba = np.empty(N, np.uint32)
+    S.terrain(N, params, seed=3, out=(xyz, rgba))
+    batches, w1, w2, w3, color, perm = pcr.pc_encode(xyz, rgba, BATCH)
+    code, where = O.verify_encoding(xyz, rgba, BATCH, batches, w1, w2, w3, color, perm)
+    assert code == 0, f"encoding differs from the definition (code {code} at {where})"
+    del xyz, rgba, perm
+    enc = O.Encoded(batches, w1, w2, w3, color, None)
+
+    W, H = 1920, 1080
+    overview = S.overview(params, W, H)
+    eyes = [S.stereo(params, 2016, 2240, e, 6.5) for e in (0, 1)]
+    with pcr.Context(0) as ctx:
+        cloud = ctx.upload_encoded(batches, w1, w2, w3, color)
+        v0 = pcr.make_view(overview, W, H, pcr.PC_VIEW_CULL)
+        pcr.pc_autotune(ctx.h, cloud, [v0])
+        [(vis0, img0)] = ctx.render(cloud, [v0])
+        pcr.pc_set_views_per_launch(ctx.h, 2)
+        stereo = [pcr.make_view(m, 2016, 2240, pcr.PC_VIEW_CULL) for m in eyes]
+        pair = ctx.render(cloud, stereo)
+        torch.cuda.synchronize()
+        stats = [ctx.stats(v) for v in range(2)]   # the stereo pair's counters
+        got = [(overview, W, H, vis0, img0)] + [(m, 2016, 2240, v, i) for m, (v, i) in zip(eyes, pair)]
+        for n, (m, w, h, vis, img) in enumerate(got):
+            ovis, ost = O.render_threaded(enc, O.make_view(m, w, h, cull=True))
+            assert (ovis != O.EMPTY).sum() > 0.2 * w * h
+            assert np.array_equal(pcr.vis_to_numpy(vis), ovis)
+            assert np.array_equal(pcr.rgba_to_numpy(img), O.resolve(ovis, enc.color))
+            if n > 0:
+                st = stats[n - 1]
+                assert st["batches_rendered"] == ost["batches_rendered"]
+                assert st["points_processed"] == ost["points_processed"]
+                assert st["batches_k"] == ost["batches_k"]
