@@ -60,3 +60,34 @@ def test_full_size_frames_bit_exact(cuda_lib):
                 assert st["batches_rendered"] == ost["batches_rendered"]
                 assert st["points_processed"] == ost["points_processed"]
                 assert st["batches_k"] == ost["batches_k"]
+
+
+def test_config2_flythrough_100m(cuda_lib):
+    """100,000,000 terrain points over 10 km, four frames of the seeded
+    120-frame fly-through at 1920x1080 with adaptive precision and culling;
+    the encoding is checked by the oracle, every frame and its counters match
+    the oracle's."""
+    import torch
+    n = 100_000_000
+    params = S.terrain_params(10000.0)
+    xyz, rgba = S.terrain(n, params, seed=2)
+    batches, w1, w2, w3, color, perm = pcr.pc_encode(xyz, rgba, BATCH)
+    code, where = O.verify_encoding(xyz, rgba, BATCH, batches, w1, w2, w3, color, perm)
+    assert code == 0, f"encoding differs from the definition (code {code} at {where})"
+    del xyz, rgba, perm
+    enc = O.Encoded(batches, w1, w2, w3, color, None)
+    W, H = 1920, 1080
+    with pcr.Context(0) as ctx:
+        cloud = ctx.upload_encoded(batches, w1, w2, w3, color)
+        for f in (0, 30, 60, 90):
+            m = S.flythrough(params, f, 120, W, H, seed=2)
+            [(vis, img)] = ctx.render(cloud, [pcr.make_view(m, W, H, pcr.PC_VIEW_CULL)])
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            ovis, ost = O.render_threaded(enc, O.make_view(m, W, H, cull=True))
+            assert np.array_equal(pcr.vis_to_numpy(vis), ovis), f"frame {f}"
+            assert np.array_equal(pcr.rgba_to_numpy(img), O.resolve(ovis, enc.color)), f"frame {f}"
+            assert st["batches_rendered"] == ost["batches_rendered"]
+            assert st["points_processed"] == ost["points_processed"]
+            assert st["batches_k"] == ost["batches_k"]
+            assert ost["batches_rendered"] < len(batches)   # the fly-through culls
