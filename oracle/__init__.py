@@ -140,6 +140,7 @@ def lib():
             L.or_render_hqs.argtypes = [vp, u64, vp, vp, vp, vp, VP, vp, vp]
             L.or_lod_render_hqs.argtypes = [vp, vp, u64, vp, vp, vp, vp, VP, f32, f32, vp, vp]
             L.or_hqs_resolve_dilated.argtypes = [vp, u32, u32, vp, vp]
+            L.or_render_hqs_threaded.argtypes = [vp, u64, vp, vp, vp, vp, VP, vp, i32, vp]
             L.or_verify_encoding.argtypes = [vp, vp, u64, u32, vp, u64, vp, vp, vp, vp, vp, i32, vp]
             _lib = L
     return _lib
@@ -393,6 +394,17 @@ def render_hqs(enc: Encoded, view: View, vis: np.ndarray):
     out = np.empty(view.width * view.height, np.uint32)
     lib().or_render_hqs(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2), _p(enc.w3),
                         _p(enc.color), ctypes.byref(view), _p(vis), _p(out))
+    return out
+
+
+def render_hqs_threaded(enc: Encoded, view: View, vis: np.ndarray, threads: int = 0):
+    """render_hqs on `threads` host threads (the same image)."""
+    import os
+    vis = np.ascontiguousarray(vis, np.uint64)
+    out = np.empty(view.width * view.height, np.uint32)
+    lib().or_render_hqs_threaded(_p(enc.batches), len(enc.batches), _p(enc.w1), _p(enc.w2),
+                                 _p(enc.w3), _p(enc.color), ctypes.byref(view), _p(vis),
+                                 int(threads or os.cpu_count() or 1), _p(out))
     return out
 
 

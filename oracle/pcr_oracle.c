@@ -796,6 +796,61 @@ void or_render_hqs(const or_batch* batches, uint64_t nbatches, const uint32_t* w
     free(sum);
 }
 
+typedef struct {
+    const or_batch* batches;
+    uint64_t lo, hi;
+    const uint32_t *w1, *w2, *w3, *color;
+    const or_view* v;
+    const uint64_t* vis;
+    uint64_t* sum;
+} hqs_job;
+
+static void* hqs_thread(void* a) {
+    hqs_job* j = (hqs_job*)a;
+    for (uint64_t b = j->lo; b < j->hi; ++b) {
+        const or_batch* B = &j->batches[b];
+        if (j->v->cull && or_cull(B, j->v)) continue;
+        int k = or_select_k(B, j->v);
+        for (uint32_t i = 0; i < B->count; ++i)
+            hqs_point(B, k, B->first + i, j->w1, j->w2, j->w3, j->color, j->v, j->vis, j->sum);
+    }
+    return NULL;
+}
+
+void or_render_hqs_threaded(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                            const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
+                            const or_view* v, const uint64_t* vis, int threads, uint32_t* out) {
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    uint64_t npix = (uint64_t)v->width * v->height;
+    hqs_job* jobs = (hqs_job*)calloc((size_t)threads, sizeof(hqs_job));
+    pthread_t* tid = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    int* ok = (int*)calloc((size_t)threads, sizeof(int));
+    for (int t = 0; t < threads; ++t) {
+        hqs_job* j = &jobs[t];
+        j->batches = batches;
+        j->lo = nbatches * (uint64_t)t / (uint64_t)threads;
+        j->hi = nbatches * (uint64_t)(t + 1) / (uint64_t)threads;
+        j->w1 = w1; j->w2 = w2; j->w3 = w3; j->color = color; j->v = v; j->vis = vis;
+        j->sum = (uint64_t*)calloc(npix ? 4 * npix : 1, sizeof(uint64_t));
+        ok[t] = pthread_create(&tid[t], NULL, hqs_thread, j) == 0;
+        if (!ok[t]) hqs_thread(j);
+    }
+    /* integer sums: adding the threads' partial sums gives the same totals */
+    for (int t = 0; t < threads; ++t) {
+        if (ok[t]) pthread_join(tid[t], NULL);
+        if (t > 0) {
+            for (uint64_t q = 0; q < 4 * npix; ++q) jobs[0].sum[q] += jobs[t].sum[q];
+            free(jobs[t].sum);
+        }
+    }
+    hqs_average(jobs[0].sum, npix, out);
+    free(jobs[0].sum);
+    free(jobs);
+    free(tid);
+    free(ok);
+}
+
 void or_lod_render_hqs(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,
                        const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
                        const uint32_t* color, const or_view* v, float lod_px,

@@ -192,6 +192,12 @@ void or_render_hqs(const or_batch* batches, uint64_t nbatches, const uint32_t* w
                    const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
                    const or_view* v, const uint64_t* vis, uint32_t* out);
 
+/* The same on `threads` threads, each summing a range of batches; the integer
+ * sums of the threads are added before the average. */
+void or_render_hqs_threaded(const or_batch* batches, uint64_t nbatches, const uint32_t* w1,
+                            const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
+                            const or_view* v, const uint64_t* vis, int threads, uint32_t* out);
+
 /* or_render_hqs for a LOD cloud: the points of the nodes that or_lod_select
  * keeps, each node at its own precision. */
 void or_lod_render_hqs(const or_batch* nodes, const uint32_t* parent, uint64_t nnodes,

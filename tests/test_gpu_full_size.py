@@ -8,8 +8,9 @@ the library's host encoder and rendered in the bench's launch configuration
 The oracle cannot sort 2B points in a test's time, but it checks the library's
 encoding against Sec. 3.1, Eq. 1 and Listing 2 in O(n). That encoding is unique,
 so an encoding that passes is the oracle's. The oracle then renders the same
-frames itself on all host cores, and every pixel of every view must match.
-About 75 GB of host memory and two minutes.
+frames itself on all host cores, and every pixel of every view must match;
+so must the overview's high-quality shading and the overview served through
+pc_submit. About 75 GB of host memory and a few minutes.
 """
 import numpy as np
 import pytest
@@ -60,6 +61,28 @@ def test_full_size_frames_bit_exact(cuda_lib):
                 assert st["batches_rendered"] == ost["batches_rendered"]
                 assert st["points_processed"] == ost["points_processed"]
                 assert st["batches_k"] == ost["batches_k"]
+            if n == 0:
+                overview_vis = ovis
+        # high-quality shading (Sec. 3.6) of the overview frame
+        pcr.pc_set_views_per_launch(ctx.h, 1)
+        vh = pcr.make_view(overview, W, H, pcr.PC_VIEW_CULL | pcr.PC_VIEW_HQS)
+        [(_, hq)] = ctx.render(cloud, [vh])
+        torch.cuda.synchronize()
+        ref = O.render_hqs_threaded(enc, O.make_view(overview, W, H, cull=True), overview_vis)
+        assert np.array_equal(pcr.rgba_to_numpy(hq), ref)
+        # the serving path: the overview through pc_submit, into library-owned
+        # and caller-owned framebuffers, equals the checked frame
+        t1 = pcr.pc_submit(ctx.h, cloud, [v0])
+        own = ctx.framebuffers([v0])
+        t2 = pcr.pc_submit(ctx.h, cloud, [v0], [(own[0][0].data_ptr(), own[0][1].data_ptr())])
+        for t in (t1, t2):
+            rc, res = pcr.pc_poll(ctx.h, t, 120_000)
+            assert rc == pcr.PC_OK and res["status"] == pcr.PC_OK
+        expect = O.resolve(overview_vis, enc.color)
+        assert np.array_equal(pcr.pc_poll(ctx.h, t1, 0)[1]["images"][0], expect)
+        assert np.array_equal(pcr.rgba_to_numpy(own[0][1]), expect)
+        for t in (t1, t2):
+            pcr.pc_release_ticket(ctx.h, t)
 
 
 def test_config2_flythrough_100m(cuda_lib):

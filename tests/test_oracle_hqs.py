@@ -159,3 +159,11 @@ def test_lod_hqs_of_the_root_alone():
     vis_root, _ = O.render(root, v)
     assert (vis == vis_root).all()
     assert (O.lod_render_hqs(lod, v, vis, 1e9) == O.render_hqs(root, v, vis)).all()
+
+
+def test_threaded_equals_single_thread():
+    enc, v = _scene(n=40000, seed=9)
+    vis, _ = O.render(enc, v)
+    ref = O.render_hqs(enc, v, vis)
+    for t in (1, 3, 8):
+        assert (O.render_hqs_threaded(enc, v, vis, threads=t) == ref).all()
