@@ -396,12 +396,14 @@ def hqs_bench(args, pcr, torch, ctx, cloud, m, plain_ms):
     return out
 
 
-def lod_bench(args, pcr, torch, ctx, params):
-    """Sec. 3.5 on the terrain: a layered octree of --lod-points points (max 12
-    levels, <= 10,240 points per node) rendered along the 120-frame fly-through
-    at 1920x1080 with nodes under 300 px culled, against brute force over the
-    same points on the same frames."""
+def lod_bench(args, pcr, torch, ctx):
+    """Sec. 3.5 on the 10 km terrain of the fly-through workload: a layered
+    octree of --lod-points points (max 12 levels, <= 10,240 points per node)
+    rendered along the 120-frame fly-through at 1920x1080 with nodes under
+    300 px culled, against brute force over the same points on the same
+    frames."""
     import pcsynth
+    params = pcsynth.terrain_params(10000.0)
     n = int(args.lod_points)
     xyz = np.empty((n, 3), np.float32)
     rgba = np.empty(n, np.uint32)
@@ -663,7 +665,7 @@ def main():
 
     lod = None
     if not args.no_lod:
-        lod = lod_bench(args, pcr, torch, ctx, params)
+        lod = lod_bench(args, pcr, torch, ctx)
         log(args, f"lod: {lod}")
 
     cpu = None

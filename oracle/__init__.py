@@ -141,6 +141,8 @@ def lib():
             L.or_lod_render_hqs.argtypes = [vp, vp, u64, vp, vp, vp, vp, VP, f32, f32, vp, vp]
             L.or_hqs_resolve_dilated.argtypes = [vp, u32, u32, vp, vp]
             L.or_render_hqs_threaded.argtypes = [vp, u64, vp, vp, vp, vp, VP, vp, i32, vp]
+            L.or_verify_lod.argtypes = [vp, vp, u64, u32, u32, u32, vp, vp, vp, u64, vp, vp, vp,
+                                        vp, vp, i32, vp]
             L.or_verify_encoding.argtypes = [vp, vp, u64, u32, vp, u64, vp, vp, vp, vp, vp, i32, vp]
             _lib = L
     return _lib
@@ -440,4 +442,23 @@ def verify_encoding(xyz, rgba, batch_size, batches, w1, w2, w3, color, perm, thr
     code = lib().or_verify_encoding(_p(xyz), _p(rgba) if rgba is not None else None, len(xyz),
                                     int(batch_size), _p(b), len(b), *(_p(a) for a in arrs),
                                     int(threads or os.cpu_count() or 1), _p(where))
+    return int(code), int(where[0])
+
+
+def verify_lod(xyz, rgba, max_levels, max_node_points, seed, nodes, parent, level, perm, w1, w2,
+               w3, color, threads=0):
+    """(code, where): 0 when the arrays are the unique LOD tree of (xyz, rgba)
+    that Sec. 3.5 defines (see or_verify_lod)."""
+    import os
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    arrs = [np.ascontiguousarray(a, np.uint32) for a in (perm, w1, w2, w3, color)]
+    nd = np.ascontiguousarray(nodes, BATCH_DTYPE)
+    par = np.ascontiguousarray(parent, np.uint32)
+    lev = np.ascontiguousarray(level, np.uint32)
+    where = np.zeros(1, np.uint64)
+    code = lib().or_verify_lod(_p(xyz), _p(rgba) if rgba is not None else None, len(xyz),
+                               int(max_levels), int(max_node_points), int(seed), _p(nd), _p(par),
+                               _p(lev), len(nd), *(_p(a) for a in arrs),
+                               int(threads or os.cpu_count() or 1), _p(where))
     return int(code), int(where[0])

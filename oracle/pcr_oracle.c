@@ -1047,3 +1047,193 @@ int or_verify_encoding(const float* xyz, const uint32_t* rgba, uint64_t n, uint3
     free(jobs);
     return code;
 }
+
+/* ---- Sec. 3.5 at full size: checking a LOD tree against the definition ---- */
+
+typedef struct { uint64_t pri; uint32_t idx; } pri_key;
+
+static int pri_less(pri_key a, pri_key b) {
+    return a.pri < b.pri || (a.pri == b.pri && a.idx < b.idx);
+}
+
+typedef struct {
+    const float* xyz;
+    const uint32_t* rgba;
+    uint64_t n;
+    uint32_t seed;
+    const or_batch* nodes;
+    const uint32_t* parent;
+    uint64_t nnodes;
+    const uint32_t *perm, *w1, *w2, *w3, *color;
+    const int* oct;          /* octant of each node in its parent (root: -1) */
+    uint64_t* seen;          /* bitmap of perm values */
+    pri_key *own_min, *own_max;
+    uint64_t lo, hi;         /* node range */
+    int code;
+    uint64_t where;
+} lod_verify_job;
+
+static int octant_of(const float* p, const or_batch* node) {
+    float half = node->size[0] * 0.5f;
+    int o = 0;
+    for (int a = 0; a < 3; ++a) o |= (p[a] >= node->min[a] + half) << a;
+    return o;
+}
+
+static void* lod_verify_nodes(void* arg) {
+    lod_verify_job* j = (lod_verify_job*)arg;
+    for (uint64_t b = j->lo; b < j->hi; ++b) {
+        const or_batch* B = &j->nodes[b];
+        uint32_t prev = 0;
+        for (uint64_t i = B->first; i < (uint64_t)B->first + B->count; ++i) {
+            uint32_t idx = j->perm[i];
+            /* a permutation, and input order within the node */
+            if ((uint64_t)idx >= j->n || (i > B->first && idx <= prev)) { j->code = 3; j->where = i; return NULL; }
+            uint64_t bit = 1ull << (idx & 63);
+            if (__atomic_fetch_or(&j->seen[idx >> 6], bit, __ATOMIC_RELAXED) & bit) {
+                j->code = 3; j->where = i; return NULL;
+            }
+            prev = idx;
+            /* routed down the octants of every ancestor */
+            const float* p = &j->xyz[3 * (uint64_t)idx];
+            for (uint64_t c = b; c != 0; c = j->parent[c])
+                if (octant_of(p, &j->nodes[j->parent[c]]) != j->oct[c]) { j->code = 4; j->where = i; return NULL; }
+            /* priorities */
+            pri_key k = {or_splitmix64(((uint64_t)j->seed << 32) + idx), idx};
+            if (i == B->first || pri_less(k, j->own_min[b])) j->own_min[b] = k;
+            if (i == B->first || pri_less(j->own_max[b], k)) j->own_max[b] = k;
+            /* Eq. 1 against the node cube, Listing 2, colour */
+            uint32_t w[3];
+            or_split_words(or_quantize30(p[0], B->min[0], B->size[0]),
+                           or_quantize30(p[1], B->min[1], B->size[1]),
+                           or_quantize30(p[2], B->min[2], B->size[2]), w);
+            if (w[0] != j->w1[i] || w[1] != j->w2[i] || w[2] != j->w3[i]) { j->code = 6; j->where = i; return NULL; }
+            if ((j->rgba ? j->rgba[idx] : 0u) != j->color[i]) { j->code = 7; j->where = i; return NULL; }
+        }
+    }
+    return NULL;
+}
+
+int or_verify_lod(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t max_levels,
+                  uint32_t max_node_points, uint32_t seed, const or_batch* nodes,
+                  const uint32_t* parent, const uint32_t* level, uint64_t nnodes,
+                  const uint32_t* perm, const uint32_t* w1, const uint32_t* w2,
+                  const uint32_t* w3, const uint32_t* color, int threads, uint64_t* where) {
+    *where = 0;
+    if (n == 0) return nnodes == 0 ? 0 : 1;
+    if (nnodes == 0 || n > 0xFFFFFFFFull || max_levels == 0 || max_node_points == 0) return 1;
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    /* the root: the cloud's corner and largest extent (the encoder's box, threaded) */
+    verify_job* bj = (verify_job*)calloc((size_t)threads, sizeof(verify_job));
+    if (!bj) return -2;
+    for (int t = 0; t < threads; ++t) {
+        bj[t].xyz = xyz;
+        bj[t].lo = n * (uint64_t)t / (uint64_t)threads;
+        bj[t].hi = n * (uint64_t)(t + 1) / (uint64_t)threads;
+    }
+    run_jobs(bj, threads, verify_box);
+    float lo[3], hi[3];
+    int have = 0;
+    for (int t = 0; t < threads; ++t) {
+        if (bj[t].hi <= bj[t].lo) continue;
+        for (int c = 0; c < 3; ++c) {
+            if (!have || bj[t].bmin[c] < lo[c]) lo[c] = bj[t].bmin[c];
+            if (!have || bj[t].bmax[c] > hi[c]) hi[c] = bj[t].bmax[c];
+        }
+        have = 1;
+    }
+    free(bj);
+    float side = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+        float e = hi[c] - lo[c];
+        if (e > side) side = e;
+    }
+    for (int c = 0; c < 3; ++c)
+        if (memcmp(&nodes[0].min[c], &lo[c], 4) != 0 || memcmp(&nodes[0].size[c], &side, 4) != 0) return 1;
+    if (parent[0] != 0 || level[0] != 0) return 2;
+    /* headers, breadth-first structure, child cubes in octant order */
+    int* oct = (int*)malloc(sizeof(int) * nnodes);
+    uint8_t* has_child = (uint8_t*)calloc(nnodes, 1);
+    int code = 0;
+    uint64_t total = 0;
+    oct[0] = -1;
+    for (uint64_t b = 0; b < nnodes && !code; ++b) {
+        if (nodes[b].first != total || nodes[b].count == 0) { code = 1; *where = b; break; }
+        total += nodes[b].count;
+        if (b == 0) continue;
+        uint32_t p = parent[b];
+        if (p >= b || (b > 1 && p < parent[b - 1]) || level[b] != level[p] + 1 || level[b] >= max_levels) {
+            code = 2; *where = b; break;
+        }
+        has_child[p] = 1;
+        float half = nodes[p].size[0] * 0.5f;
+        int o = 0;
+        for (int c = 0; c < 3; ++c) {
+            float mid = nodes[p].min[c] + half;
+            if (memcmp(&nodes[b].min[c], &mid, 4) == 0) o |= 1 << c;
+            else if (memcmp(&nodes[b].min[c], &nodes[p].min[c], 4) != 0) { code = 2; *where = b; }
+            if (memcmp(&nodes[b].size[c], &half, 4) != 0) { code = 2; *where = b; }
+        }
+        oct[b] = o;
+        if (b > 1 && parent[b - 1] == p && oct[b - 1] >= o) { code = 2; *where = b; }
+    }
+    if (!code && total != n) { code = 1; *where = nnodes; }
+    /* the split rule: a node splits, keeping max_node_points points, exactly when
+     * it holds more than that and is above the last level */
+    for (uint64_t b = 0; b < nnodes && !code; ++b) {
+        int last = level[b] + 1 >= max_levels;
+        if (has_child[b] ? (nodes[b].count != max_node_points || last)
+                         : (nodes[b].count > max_node_points && !last)) { code = 5; *where = b; }
+    }
+    pri_key* own_min = (pri_key*)malloc(sizeof(pri_key) * nnodes);
+    pri_key* own_max = (pri_key*)malloc(sizeof(pri_key) * nnodes);
+    uint64_t* seen = (uint64_t*)calloc((size_t)((n + 63) / 64), sizeof(uint64_t));
+    if (!code) {
+        lod_verify_job* jobs = (lod_verify_job*)calloc((size_t)threads, sizeof(lod_verify_job));
+        pthread_t* tid = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+        int* ok = (int*)calloc((size_t)threads, sizeof(int));
+        for (int t = 0; t < threads; ++t) {
+            lod_verify_job* j = &jobs[t];
+            j->xyz = xyz; j->rgba = rgba; j->n = n; j->seed = seed;
+            j->nodes = nodes; j->parent = parent; j->nnodes = nnodes;
+            j->perm = perm; j->w1 = w1; j->w2 = w2; j->w3 = w3; j->color = color;
+            j->oct = oct; j->seen = seen; j->own_min = own_min; j->own_max = own_max;
+            j->lo = nnodes * (uint64_t)t / (uint64_t)threads;
+            j->hi = nnodes * (uint64_t)(t + 1) / (uint64_t)threads;
+            ok[t] = pthread_create(&tid[t], NULL, lod_verify_nodes, j) == 0;
+            if (!ok[t]) lod_verify_nodes(j);
+        }
+        for (int t = 0; t < threads; ++t) {
+            if (ok[t]) pthread_join(tid[t], NULL);
+            if (!code && jobs[t].code) { code = jobs[t].code; *where = jobs[t].where; }
+        }
+        free(jobs);
+        free(tid);
+        free(ok);
+    }
+    /* priorities: a node's own points all come before every point below it */
+    if (!code) {
+        pri_key* sub = (pri_key*)malloc(sizeof(pri_key) * nnodes);    /* min over the subtree */
+        pri_key* below = (pri_key*)malloc(sizeof(pri_key) * nnodes);  /* min over the descendants */
+        uint8_t* any = (uint8_t*)calloc(nnodes, 1);
+        for (uint64_t b = 0; b < nnodes; ++b) sub[b] = own_min[b];
+        for (uint64_t b = nnodes - 1; b >= 1; --b) {
+            uint32_t p = parent[b];
+            if (pri_less(sub[b], sub[p])) sub[p] = sub[b];
+            if (!any[p] || pri_less(sub[b], below[p])) below[p] = sub[b];
+            any[p] = 1;
+        }
+        for (uint64_t b = 0; b < nnodes && !code; ++b)
+            if (any[b] && !pri_less(own_max[b], below[b])) { code = 5; *where = b; }
+        free(sub);
+        free(below);
+        free(any);
+    }
+    free(seen);
+    free(own_min);
+    free(own_max);
+    free(oct);
+    free(has_child);
+    return code;
+}

@@ -225,6 +225,25 @@ int or_verify_encoding(const float* xyz, const uint32_t* rgba, uint64_t n, uint3
                        const uint32_t* w2, const uint32_t* w3, const uint32_t* color,
                        const uint32_t* perm, int threads, uint64_t* where);
 
+/* Check a LOD tree of n input points against Sec. 3.5 as or_lod_build builds
+ * it, in O(n * depth) on `threads` threads: the root cube (the points' corner
+ * and largest extent), breadth-first numbering with each child the cube of
+ * its octant (children in octant order), every point routed down the octants
+ * of all its ancestors, the split rule (a node keeps max_node_points points
+ * and has children exactly when it held more and is above the last level),
+ * every own point of a node before every point below it in (SplitMix64
+ * priority, index) order, input order within a node, a permutation, and Eq. 1
+ * against the node cube with Listing 2 and the colours. The tree is unique, so
+ * one that passes is or_lod_build's. Returns 0, or the first failure found:
+ * 1 header/root, 2 structure, 3 permutation/order, 4 octant, 5 split or
+ * priority rule, 6 words, 7 colour, with its node or point in *where; -2 when
+ * out of memory. */
+int or_verify_lod(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t max_levels,
+                  uint32_t max_node_points, uint32_t seed, const or_batch* nodes,
+                  const uint32_t* parent, const uint32_t* level, uint64_t nnodes,
+                  const uint32_t* perm, const uint32_t* w1, const uint32_t* w2,
+                  const uint32_t* w3, const uint32_t* color, int threads, uint64_t* where);
+
 /* Sec. 3.3 visibility buffer: out[p] = colour of the winning point, 0 where
  * no point landed. */
 void or_resolve(const uint64_t* vis, uint64_t npixels, const uint32_t* color,

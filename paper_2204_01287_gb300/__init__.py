@@ -275,12 +275,13 @@ def pc_build_lod(ctx: int, cloud: int, max_levels: int = 12, max_node_points: in
 
 
 def pc_lod_encode(xyz: np.ndarray, rgba, max_levels: int = 12, max_node_points: int = 10240,
-                  seed: int = 0, threads: int = 0):
-    """Host LOD builder: (nodes, parent, level, perm, w1, w2, w3, color)."""
+                  seed: int = 0, threads: int = 0, max_nodes: int | None = None):
+    """Host LOD builder: (nodes, parent, level, perm, w1, w2, w3, color).
+    max_nodes bounds the node arrays (default: one per point)."""
     xyz = np.ascontiguousarray(xyz, np.float32)
     n = xyz.shape[0]
     rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
-    cap = max(n, 1)
+    cap = max(int(max_nodes) if max_nodes else n, 1)
     nodes = np.zeros(cap, BATCH_DTYPE)
     parent = np.zeros(cap, np.uint32)
     level = np.zeros(cap, np.uint32)

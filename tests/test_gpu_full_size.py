@@ -114,3 +114,54 @@ def test_config2_flythrough_100m(cuda_lib):
             assert st["points_processed"] == ost["points_processed"]
             assert st["batches_k"] == ost["batches_k"]
             assert ost["batches_rendered"] < len(batches)   # the fly-through culls
+
+
+def test_config4_lod_1b(cuda_lib):
+    """Config 4 at full size: 1,000,000,000 points of the 10 km terrain as a
+    layered octree (12 levels, <= 10,240 points per node), built on the device
+    by pc_build_lod. The oracle checks the source encoding and the tree against
+    their definitions. The device tree must equal the host builder's, and LOD
+    frames of the fly-through at 1080p, with thresholds of 300 and 100 px, must
+    match the oracle's LOD renders with their counters."""
+    import torch
+    n = 1_000_000_000
+    params = S.terrain_params(10000.0)
+    xyz = np.empty((n, 3), np.float32)
+    rgba = np.empty(n, np.uint32)
+    S.terrain(n, params, seed=10, out=(xyz, rgba))
+    batches, w1, w2, w3, color, perm = pcr.pc_encode(xyz, rgba, BATCH)
+    code, where = O.verify_encoding(xyz, rgba, BATCH, batches, w1, w2, w3, color, perm)
+    assert code == 0, f"encoding differs from the definition (code {code} at {where})"
+    del xyz, rgba, perm
+    enc = O.Encoded(batches, w1, w2, w3, color, None)
+    # the LOD builder's input: the source decoded at k = 3 (Sec. 3.3)
+    dec = O.decode_cloud(enc, 3)
+    tree = pcr.pc_lod_encode(dec, color, 12, 10240, 0, max_nodes=n // 1000 + 65536)
+    nodes, parent, level, lperm, l1, l2, l3, lc = tree
+    code, where = O.verify_lod(dec, color, 12, 10240, 0, nodes, parent, level, lperm, l1, l2, l3, lc)
+    assert code == 0, f"LOD tree differs from the definition (code {code} at {where})"
+    del dec
+    ref = O.LodCloud(nodes, parent, level, l1, l2, l3, lc, lperm)
+    W, H = 1920, 1080
+    with pcr.Context(0) as ctx:
+        src = ctx.upload_encoded(batches, w1, w2, w3, color)
+        lod = pcr.pc_build_lod(ctx.h, src, 12, 10240, 0)
+        pcr.pc_release_cloud(ctx.h, src)
+        d_nodes, d1, d2, d3, dc = pcr.pc_cloud_download(ctx.h, lod)
+        assert d_nodes.tobytes() == nodes.tobytes()
+        for a, b in ((d1, l1), (d2, l2), (d3, l3), (dc, lc)):
+            assert np.array_equal(a, b)
+        del d1, d2, d3, dc
+        for f in (0, 45, 90):
+            m = S.flythrough(params, f, 120, W, H, seed=3)
+            for lod_px in (300.0, 100.0):
+                [(vis, img)] = ctx.render(lod, [pcr.make_view(m, W, H, pcr.PC_VIEW_CULL, lod_px)])
+                torch.cuda.synchronize()
+                st = ctx.stats()
+                ovis, ost = O.lod_render(ref, O.make_view(m, W, H), lod_px)
+                assert np.array_equal(pcr.vis_to_numpy(vis), ovis), f"frame {f}, {lod_px} px"
+                assert np.array_equal(pcr.rgba_to_numpy(img), O.resolve(ovis, lc))
+                assert st["batches_rendered"] == ost["batches_rendered"]
+                assert st["points_processed"] == ost["points_processed"]
+                assert st["batches_k"] == ost["batches_k"]
+                assert (ovis != O.EMPTY).sum() > 0.1 * W * H

@@ -73,6 +73,14 @@ VERIFY_MUTANTS = [
      "if (0) {"),
     ("verify_no_range", "if ((uint64_t)idx >= j->n) { j->code = 2; j->where = i; return NULL; }",
      "if (0) { j->code = 2; j->where = i; return NULL; }"),
+    ("verify_lod_no_octant",
+     "if (octant_of(p, &j->nodes[j->parent[c]]) != j->oct[c]) { j->code = 4; j->where = i; return NULL; }",
+     ";"),
+    ("verify_lod_no_priority", "if (any[b] && !pri_less(own_max[b], below[b])) { code = 5; *where = b; }",
+     ";"),
+    ("verify_lod_no_split_rule", "                         : (nodes[b].count > max_node_points && !last)) { code = 5; *where = b; }",
+     "                         : 0) { code = 5; *where = b; }"),
+    ("verify_lod_no_order", "(i > B->first && idx <= prev)", "(0)"),
 ]
 
 CASES = ([m + ("test_oracle_pins.py",) for m in MUTANTS] +

@@ -75,3 +75,84 @@ def test_rejects_an_unsorted_encoding(cloud):
     perm = np.arange(len(xyz), dtype=np.uint32)
     assert O.verify_encoding(xyz, rgba, BS, enc.batches, enc.w1, enc.w2, enc.w3, enc.color,
                              perm)[0] == 3
+
+
+# ---- the LOD tree checker (Sec. 3.5) ------------------------------------------------
+
+L, M, SEED = 12, 700, 5
+
+
+@pytest.fixture(scope="module")
+def tree():
+    p = S.terrain_params(3000.0, 0.15, 80)
+    xyz, rgba = S.terrain(50000, p, seed=13)
+    return xyz, rgba, O.lod_build(xyz, rgba, L, M, SEED)
+
+
+def _lod(xyz, rgba, t, levels=L, m=M, seed=SEED, **over):
+    a = dict(nodes=t.nodes.copy(), parent=t.parent.copy(), level=t.level.copy(), perm=t.perm.copy(),
+             w1=t.w1.copy(), w2=t.w2.copy(), w3=t.w3.copy(), color=t.color.copy())
+    a.update(over)
+    return O.verify_lod(xyz, rgba, levels, m, seed, a["nodes"], a["parent"], a["level"], a["perm"],
+                        a["w1"], a["w2"], a["w3"], a["color"], threads=3)
+
+
+def test_lod_accepts_the_oracle_tree(tree):
+    xyz, rgba, t = tree
+    assert len(t.nodes) > 20 and t.level.max() >= 2
+    assert _lod(xyz, rgba, t) == (0, 0)
+
+
+def test_lod_rejects_wrong_parameters(tree):
+    xyz, rgba, t = tree
+    assert _lod(xyz, rgba, t, seed=SEED + 1)[0] == 5      # another priority order
+    assert _lod(xyz, rgba, t, m=M + 1)[0] == 5            # another split size
+    assert _lod(xyz, rgba, t, levels=int(t.level.max()))[0] == 2
+
+
+def test_lod_rejects_structure_mistakes(tree):
+    xyz, rgba, t = tree
+    nd = t.nodes.copy()
+    nd[0]["size"][0] *= np.float32(1.5)
+    assert _lod(xyz, rgba, t, nodes=nd)[0] == 1
+    b = int(np.nonzero(t.level == 2)[0][0])
+    par = t.parent.copy()
+    par[b] = 0
+    assert _lod(xyz, rgba, t, parent=par)[0] == 2
+    nd = t.nodes.copy()
+    nd[b]["min"][0] = np.nextafter(nd[b]["min"][0], np.float32(np.inf))
+    assert _lod(xyz, rgba, t, nodes=nd) == (2, b)
+    # the first points of two sibling nodes exchanged (with their words and
+    # colours): each now sits in the wrong octant of the root
+    kids = np.nonzero(t.parent == 0)[0][1:]
+    i, j = int(t.nodes[kids[0]]["first"]), int(t.nodes[kids[1]]["first"])
+    sw = {k: getattr(t, k).copy() for k in ("perm", "w1", "w2", "w3", "color")}
+    for a in sw.values():
+        a[[i, j]] = a[[j, i]]
+    assert _lod(xyz, rgba, t, **sw) == (4, i)
+
+
+def test_lod_rejects_order_word_and_colour_mistakes(tree):
+    xyz, rgba, t = tree
+    f = int(t.nodes[3]["first"])
+    # two points of a node exchanged with their words and colours: only the
+    # input order within the node is broken
+    sw = {k: getattr(t, k).copy() for k in ("perm", "w1", "w2", "w3", "color")}
+    for a in sw.values():
+        a[[f, f + 1]] = a[[f + 1, f]]
+    assert _lod(xyz, rgba, t, **sw) == (3, f + 1)
+    for name, code in (("w1", 6), ("w3", 6), ("color", 7)):
+        w = getattr(t, name).copy()
+        w[f + 2] ^= 1 << 12
+        assert _lod(xyz, rgba, t, **{name: w}) == (code, f + 2)
+
+
+def test_lod_rejects_a_leaf_that_should_have_split(tree):
+    """A tree cut at 3 levels keeps more than M points in its deepest leaves;
+    under a 12-level rule those leaves should have split."""
+    xyz, rgba, _ = tree
+    t3 = O.lod_build(xyz, rgba, 3, M, SEED)
+    assert _lod(xyz, rgba, t3, levels=3) == (0, 0)
+    assert (t3.nodes["count"][t3.level == 2] > M).any()
+    code, b = _lod(xyz, rgba, t3, levels=L)
+    assert code == 5 and t3.level[b] == 2 and t3.nodes[b]["count"] > M
