@@ -574,13 +574,15 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    # one event per frame boundary (the first and last bracket the timed region)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
         ctx.render(cloud, [view], fbs)
-    e1.record(stream)
+        evs[i + 1].record(stream)
+    e0, e1 = evs[0], evs[-1]
     torch.cuda.synchronize()
+    frame_ms = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
@@ -598,7 +600,11 @@ def main():
                 "kernel": "k_raster", "kernel_ms": raster_ms,
                 "algorithmic_bytes": raster_bytes, "peak_source": peak_kind}
     frame_bytes = raster_bytes + 16 * W * H + 4 * W * H
-    passes = {"clear_ms": timing.ms_clear / max(1, timing.frames),
+    passes = {"frame_ms_median": float(np.median(frame_ms)),
+              "frame_ms_p10_p90": [float(np.percentile(frame_ms, 10)),
+                                   float(np.percentile(frame_ms, 90))],
+              "all_points_per_s_g": n / (float(np.median(frame_ms)) / 1e3) / 1e9,
+              "clear_ms": timing.ms_clear / max(1, timing.frames),
               "cull_ms": timing.ms_cull / max(1, timing.frames),
               "raster_ms": raster_ms,
               "resolve_ms": timing.ms_resolve / max(1, timing.frames),
@@ -671,8 +677,9 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         pps, cores, desc, _, _ = cpu_baseline(args, params, m, args.cpu_sample)
+        pps1, _, desc1, _, _ = cpu_baseline(args, params, m, min(args.cpu_sample, 2e6), threads=1)
         cpu = {"value": pps / 1e9, "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
-               "sample": desc}
+               "sample": desc, "single_thread": {"value": pps1 / 1e9, "sample": desc1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world,
