@@ -42,6 +42,7 @@ METRIC = "Gpoints/s & ms/frame at 2B pts 1080p; %HBM peak; batched views/s, p50/
 # DRAM bytes (read + write) of one k_raster1 launch in the ncu capture of the
 # 50M-point overview (the summary under profiles/); the traffic of the bench's
 # launch is this scaled by the points processed. Re-capture when the kernel changes.
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
 RASTER_CAPTURE_POINTS = 50_000_000
 RASTER_CAPTURE_DRAM_BYTES = 210_066_944
 
@@ -68,6 +69,7 @@ def parse():
     ap.add_argument("--no-multiview", action="store_true")
     ap.add_argument("--no-order", action="store_true")
     ap.add_argument("--no-hqs", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--order-points", type=float, default=2e8)
     ap.add_argument("--lod-points", type=float, default=1e9)
     ap.add_argument("--verbose", action="store_true")
@@ -272,6 +274,59 @@ def serving_bench(args, pcr, ctx, clouds):
             "one_view_per_launch": single,
             "speedup_vs_one_view_per_launch": batched["views_per_s"] / single["views_per_s"],
             "identical_bits": hb == hs, "all_ok": batched["ok"] and single["ok"]}
+
+
+def small_configs_bench(args, pcr, torch, ctx):
+    """The two smaller workloads: 1M points in the unit cube at 512x512 with
+    k forced to 3 and no culling, and 100M points of the 10 km terrain along
+    the 120-frame fly-through at 1080p with adaptive precision and culling.
+    CUDA events over all frames."""
+    import pcsynth
+    out = {}
+    xyz, rgba = pcsynth.unit_cube(1_000_000, seed=0)
+    cube = ctx.upload(xyz, rgba)
+    v = pcr.make_view(pcsynth.cube_camera(512, 512), 512, 512, pcr.PC_VIEW_FORCE_K(3))
+    fbs = ctx.framebuffers([v])
+    for _ in range(5):
+        ctx.render(cube, [v], fbs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(200):
+        ctx.render(cube, [v], fbs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 200
+    out["cube_1m_512_k3"] = {"ms_per_frame": ms, "gpoints_per_s": 1e6 / (ms / 1e3) / 1e9}
+    pcr.pc_release_cloud(ctx.h, cube)
+    params = pcsynth.terrain_params(10000.0)
+    n = 100_000_000
+    xyz = np.empty((n, 3), np.float32)
+    rgba = np.empty(n, np.uint32)
+    pcsynth.terrain(n, params, seed=args.seed + 1, out=(xyz, rgba))
+    terr = ctx.upload(xyz, rgba)
+    del xyz, rgba
+    W, H = args.width, args.height
+    views = [pcr.make_view(pcsynth.flythrough(params, f, 120, W, H, seed=args.seed), W, H,
+                           pcr.PC_VIEW_CULL) for f in range(120)]
+    fbs = ctx.framebuffers(views[:1])
+    for v in views[:5]:
+        ctx.render(terr, [v], fbs)
+    pts = 0
+    for v in views[::10]:
+        ctx.render(terr, [v], fbs)
+        pts += ctx.stats()["points_processed"]
+    e0.record()
+    for v in views:
+        ctx.render(terr, [v], fbs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / len(views)
+    out["terrain_100m_flythrough_1080p"] = {
+        "ms_per_frame": ms, "points_processed_avg": pts / len(views[::10]),
+        "gpoints_per_s": pts / len(views[::10]) / (ms / 1e3) / 1e9,
+        "all_points_per_s_g": n / (ms / 1e3) / 1e9}
+    pcr.pc_release_cloud(ctx.h, terr)
+    return out
 
 
 def multiview_bench(args, pcr, torch, ctx, cloud, params):
@@ -598,7 +653,10 @@ def main():
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_source": "ncu capture of the 50M-point overview, scaled by points processed",
                 "kernel": "k_raster", "kernel_ms": raster_ms,
-                "algorithmic_bytes": raster_bytes, "peak_source": peak_kind}
+                "algorithmic_bytes": raster_bytes, "peak_source": peak_kind,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
+                "atomic_min_per_frame": st["points_atomic"],
+                "atomic_min_per_s_g": st["points_atomic"] / (raster_ms / 1e3) / 1e9}
     frame_bytes = raster_bytes + 16 * W * H + 4 * W * H
     passes = {"frame_ms_median": float(np.median(frame_ms)),
               "frame_ms_p10_p90": [float(np.percentile(frame_ms, 10)),
@@ -654,6 +712,11 @@ def main():
         serving = serving_bench(args, pcr, ctx, clouds)
         log(args, f"serving: {serving}")
 
+    small = None
+    if not args.no_small:
+        small = small_configs_bench(args, pcr, torch, ctx)
+        log(args, f"small configs: {small}")
+
     multiview = None
     if not args.no_multiview:
         multiview = multiview_bench(args, pcr, torch, ctx, cloud, params)
@@ -696,6 +759,7 @@ def main():
                            "setup_s": {"generate": t_gen, "encode_upload": t_up}},
                 "roofline": roofline, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
                 "multiview": multiview, "serving": serving, "lod": lod, "hqs": hqs,
+                "small_configs": small,
                 "vertex_order": order, "autotune": tune,
                 "gpu_launches": int(timing.launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
