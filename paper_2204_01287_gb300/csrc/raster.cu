@@ -1,22 +1,29 @@
 // raster.cu — sm_103a kernels of the point rasterizer.
 //
-//   k_clear    visibility buffers <- all ones; scratch counters <- 0
-//   k_cull     per batch and view: conservative frustum culling (Sec. 3.2) and
-//              the precision k from the projected batch extent (Sec. 3.3);
-//              surviving batches are appended, in segments of up to
-//              kSegmentPoints points, to a draw list
-//   k_raster   persistent warps take draw-list segments, load the k coordinate
-//              words of 4 consecutive points with one 16-byte load per word
-//              (Sec. 3.4), decode, project (Listing 1), do the non-atomic
-//              early-depth test and atomicMin the 64-bit key; one pass serves
-//              every view of the launch (Sec. 3.7)
-//   k_resolve  visibility key -> colour of the winning point (Sec. 3.3)
+//   k_clear     visibility buffers <- all ones (and shading sums <- 0); scratch
+//               counters <- 0
+//   k_lod_pass  LOD clouds: per node and view, frustum, projected extent and
+//               (foveated) threshold (Sec. 3.5, 3.7)
+//   k_cull      per batch and view: conservative frustum culling (Sec. 3.2) and
+//               the precision k from the projected batch extent (Sec. 3.3);
+//               surviving batches are appended, in segments, to a draw list
+//   k_raster    persistent warps take draw-list segments, load the k coordinate
+//               words of 4 consecutive points with one 16-byte load per word
+//               (Sec. 3.4), decode, project (Listing 1), do the non-atomic
+//               early-depth test and atomicMin the 64-bit key; one pass serves
+//               every view of the launch (Sec. 3.7)
+//   k_shade     high-quality shading (Sec. 3.6): the colour pass over the same
+//               draw list, summing the colours of the points within 1% of their
+//               pixel's closest depth
+//   k_resolve   visibility key -> colour of the winning point (Sec. 3.3), the
+//               average of the sums (Sec. 3.6), depth-aware dilation (Sec. 3.7)
 //
 // Bit-exactness: every float operation that decides a key or a pixel is an
 // explicit round-to-nearest intrinsic in the same order as the CPU oracle's
 // definition (decode x = min + float(X) * cell; c = ((m0 x + m4 y) + m8 z) +
-// m12; f = ((c / w) * 0.5 + 0.5) * W with an IEEE divide). The file is also
-// compiled with --fmad=false so nothing else is contracted.
+// m12; f = ((c / w) * 0.5 + 0.5) * W with an IEEE divide), or a packed f32x2
+// instruction that rounds each half the same way. The file is also compiled
+// with --fmad=false so nothing else is contracted.
 #include <cstdint>
 
 #include "pc_internal.h"
@@ -71,13 +78,6 @@ __device__ __forceinline__ float clip_row(const float* m, int r, float x, float 
     return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[r], x), __fmul_rn(m[r + 4], y)),
                                __fmul_rn(m[r + 8], z)),
                      m[r + 12]);
-}
-
-// The same for a row stored contiguously (r0, r1, r2, r3).
-__device__ __forceinline__ float clip_row4(const float* r, float x, float y, float z) {
-    return __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)),
-                               __fmul_rn(r[2], z)),
-                     r[3]);
 }
 
 // Unfloored pixel coordinate from a clip coordinate: ((c / w) * 0.5 + 0.5) * W.
