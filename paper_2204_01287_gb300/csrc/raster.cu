@@ -496,9 +496,10 @@ __device__ __forceinline__ f2_t f2_fma_rd(f2_t a, f2_t b, f2_t c) {
 //
 // Every lane takes an aligned group of 4 consecutive points (one 16-byte load
 // per coordinate word, Sec. 3.4): it decodes and projects all four, then issues
-// the four early-depth reads back to back, then compares and updates. All
+// the early-depth reads back to back, then compares and updates. All
 // arithmetic that decides a key or a pixel uses round-to-nearest intrinsics that
-// are never contracted (__fmul_rn, __fadd_rn), in the oracle's order.
+// are never contracted (__fmul_rn, __fadd_rn), or packed f32x2 instructions that
+// no packed multiply feeds, in the oracle's order.
 
 // Per-view constants.
 struct ViewConst {
@@ -527,9 +528,10 @@ __device__ __forceinline__ ViewConst make_view_const(const ViewParams& v) {
 }
 
 // The clip coordinates of one point (Listing 1), each row as
-// ((m[r] x + m[r+4] y) + m[r+8] z) + m[r+12]. The x and y rows share their
-// products' operands, so their products are packed pairs; the sums are scalar
-// adds, except the last one, whose operands are sums.
+// ((m[r] x + m[r+4] y) + m[r+8] z) + m[r+12]. The x and y rows' products of
+// one coordinate form a packed pair ((m0 x, m1 x), ...), as do the w row's
+// first two; the sums are scalar adds, except the last one of the x and y rows,
+// whose operands are sums.
 __device__ __forceinline__ void clip_xyw(const ViewConst& vc, float x, float y, float z, float& cx,
                                          float& cy, float& cw) {
     float a0, a1, b0, b1, c0, c1, w0, w1;
