@@ -1075,13 +1075,16 @@ __device__ __forceinline__ uint32_t shade_segment_k(const CloudView& c, const Vi
 
 // Persistent warps take draw-list segments (a counter of their own); each
 // segment is walked once per shaded view that did not cull its batch.
-// FALLBACK: the second pass for packed views, which returns at once unless
-// one of its views flagged a pixel.
+// LAYOUTS: the sum layouts of the launch's shaded views (1 two-word, 2 packed,
+// 3 both), so that a launch of one layout carries only its own code; 0 is the
+// second pass for packed views, which returns at once unless one of its views
+// flagged a pixel.
 // (No __launch_bounds__: with it ptxas held this kernel to 32 registers and
 // spilled.)
-template <bool FALLBACK>
+template <int LAYOUTS>
 __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s,
                         uint32_t shade_mask) {
+    constexpr bool FALLBACK = LAYOUTS == 0;
     __shared__ uint32_t sh_blend[kMaxViewsPerLaunch];
     if (FALLBACK) {
         uint32_t fb = 0;
@@ -1124,7 +1127,7 @@ __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s
             if (FALLBACK)
                 n = shade_segment_k<ShadeMode::kFallback>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
                                                           lane);
-            else if (vp.flags & PC_VIEW_HQS_PACKED)
+            else if (LAYOUTS == 2 || (LAYOUTS == 3 && (vp.flags & PC_VIEW_HQS_PACKED)))
                 n = shade_segment_k<ShadeMode::kPacked>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
                                                         lane);
             else
@@ -1302,13 +1305,13 @@ cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view
     return cudaGetLastError();
 }
 
-template <bool FALLBACK>
+template <int LAYOUTS>
 static cudaError_t launch_shade_kernel(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                                        Scratch s, int threads, uint32_t mask, cudaStream_t st) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<FALLBACK>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<LAYOUTS>, threads, 0);
     const int blocks = num_sms() * (nb > 0 ? nb : 1);
-    k_shade<FALLBACK><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
+    k_shade<LAYOUTS><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
     return cudaGetLastError();
 }
 
@@ -1324,10 +1327,13 @@ cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_
     if (!mask) return cudaSuccess;
     int threads = shape.threads_per_block > 0 ? shape.threads_per_block : kRasterThreads;
     threads = threads > kRasterThreads ? kRasterThreads : (threads < 32 ? 32 : threads & ~31);
-    cudaError_t e = launch_shade_kernel<false>(c, vt, view_base, s, threads, mask, st);
+    const int layouts = (mask != packed ? 1 : 0) | (packed ? 2 : 0);
+    cudaError_t e = layouts == 1 ? launch_shade_kernel<1>(c, vt, view_base, s, threads, mask, st)
+                  : layouts == 2 ? launch_shade_kernel<2>(c, vt, view_base, s, threads, mask, st)
+                                 : launch_shade_kernel<3>(c, vt, view_base, s, threads, mask, st);
     *launched = 1;
     if (e != cudaSuccess || !packed) return e;
-    e = launch_shade_kernel<true>(c, vt, view_base, s, threads, packed, st);
+    e = launch_shade_kernel<0>(c, vt, view_base, s, threads, packed, st);
     *launched = 2;
     return e;
 }
