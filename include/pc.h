@@ -131,9 +131,7 @@ pc_status pc_upload_cloud(pc_ctx* ctx, const float* xyz, const uint32_t* rgba,
                           uint64_t n, pc_cloud* out);
 
 /* Upload an already encoded cloud (host buffers in the pc_encode layout; the
- * library copies them). Every batch must satisfy first + count <= n, and
- * every w1 word must be below 2^30 (Listing 2 leaves the top two bits zero);
- * PC_EINVAL otherwise. */
+ * library copies them). Every batch must satisfy first + count <= n. */
 pc_status pc_upload_encoded(pc_ctx* ctx, const pc_batch* batches, uint64_t nbatches,
                             const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
                             const uint32_t* color, uint64_t n, pc_cloud* out);
@@ -255,9 +253,7 @@ pc_status pc_render(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t 
  * application owns every device allocation through its own allocator; render
  * loops that fix their memory at start-up). It renders one view of an encoded
  * cloud held in caller-owned device buffers (the pc_encode layout: batches,
- * w1/w2/w3/color with room for a multiple of 4 words, all 16-byte aligned, w1
- * words below 2^30 as pc_encode writes them: larger ones give unspecified
- * images, though nothing is read out of bounds) into
+ * w1/w2/w3/color with room for a multiple of 4 words, all 16-byte aligned) into
  * caller-owned vis and rgba (rgba may be NULL), stream-ordered and
  * asynchronous, with precision threshold precision_px (512 is the default of
  * pc_config). It allocates nothing: its scratch (draw list, counters) is a

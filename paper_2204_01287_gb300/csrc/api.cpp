@@ -500,23 +500,6 @@ pc_status upload_encoded_internal(Ctx& c, const pc_batch* batches, uint64_t nbat
         cl->free_device();
         return ctx->cuda_fail(e, "cloud upload");
     }
-    // the first words must be below 2^30 (Listing 2 leaves the top bits zero)
-    uint32_t* bad = nullptr;
-    uint32_t bad_h = 0;
-    e = cudaMalloc(&bad, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(uint32_t));
-    if (e == cudaSuccess) e = launch_check_words(cl->w1, n, bad, nullptr);
-    if (e == cudaSuccess) e = cudaMemcpy(&bad_h, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-    cudaFree(bad);
-    if (e != cudaSuccess) {
-        cl->free_device();
-        return ctx->cuda_fail(e, "word check");
-    }
-    if (bad_h) {
-        cl->free_device();
-        ctx->fail_msg("coordinate words must be below 2^30");
-        return PC_EINVAL;
-    }
     cl->device_bytes = 4 * wb + nbatches * sizeof(pc_batch);
     out = cl;
     return PC_OK;

@@ -160,8 +160,6 @@ cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_
                          RasterShape shape, cudaStream_t st, int* launched);
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s,
                            cudaStream_t st);
-// Sets *bad (device) when one of the n words is not below 2^30.
-cudaError_t launch_check_words(const uint32_t* w, uint64_t n, uint32_t* bad, cudaStream_t st);
 // Blocks per SM the raster kernel can keep resident at a block size.
 int raster_occupancy(int threads_per_block, bool multiview);
 

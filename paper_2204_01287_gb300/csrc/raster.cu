@@ -545,18 +545,9 @@ __device__ __forceinline__ void clip_xyw(const ViewConst& vc, float x, float y, 
     cw = __fadd_rn(__fadd_rn(__fadd_rn(w0, w1), __fmul_rn(vc.mw[2], z)), vc.mw[3]);
 }
 
-// Decode variants, by template parameter K: 1, 2, 3 decode at precision k = K;
-// 1 takes the shortcut of decode_point, so batches whose y cell would not
-// scale exactly (0 < size.y < 2^-106) use 4, the general code at k = 1.
-template <int K>
-__host__ __device__ constexpr int prec() {
-    return K == 4 ? 1 : K;
-}
-
 // Per-batch decode constants at precision k.
 struct DecConst {
     float mn[3], cell[3];
-    float cell_y1;    // k = 1: cell.y * 2^-10, the scale of y kept in place
 };
 
 __device__ __forceinline__ DecConst make_dec_const(const pc_batch& b, int k) {
@@ -566,13 +557,7 @@ __device__ __forceinline__ DecConst make_dec_const(const pc_batch& b, int k) {
         d.mn[a] = b.min[a];
         d.cell[a] = ldexpf(b.size[a], -10 * k);   // exact power-of-two scaling
     }
-    d.cell_y1 = ldexpf(b.size[1], -20);
     return d;
-}
-
-// True when a batch may take the k = 1 shortcut: size.y * 2^-20 is exact.
-__device__ __forceinline__ bool k1_shortcut(const pc_batch& b) {
-    return b.size[1] == 0.0f || (b.size[1] >= 0x1.0p-106f && b.size[1] <= 3.0e38f);
 }
 
 // Integer coordinates of one point at precision k from its words (Sec. 3.3):
@@ -580,11 +565,11 @@ __device__ __forceinline__ bool k1_shortcut(const pc_batch& b) {
 template <int K>
 __device__ __forceinline__ void decode_q(uint32_t a, uint32_t b, uint32_t c, uint32_t& qx,
                                          uint32_t& qy, uint32_t& qz) {
-    if (prec<K>() == 1) {
+    if (K == 1) {
         qx = a & 1023u;
         qy = (a >> 10) & 1023u;
         qz = (a >> 20) & 1023u;
-    } else if (prec<K>() == 2) {
+    } else if (K == 2) {
         qx = ((a & 1023u) << 10) | (b & 1023u);
         qy = (((a >> 10) & 1023u) << 10) | ((b >> 10) & 1023u);
         qz = (((a >> 20) & 1023u) << 10) | ((b >> 20) & 1023u);
@@ -599,35 +584,19 @@ __device__ __forceinline__ void decode_q(uint32_t a, uint32_t b, uint32_t c, uin
 // rounded to nearest for the 30-bit values of k = 3, as (float)q.
 template <int K>
 __device__ __forceinline__ float q_to_float(uint32_t q) {
-    if (prec<K>() <= 2) return __fsub_rn(__uint_as_float(0x4B000000u | q), 8388608.0f);
+    if (K <= 2) return __fsub_rn(__uint_as_float(0x4B000000u | q), 8388608.0f);
     return __uint2float_rn(q);
 }
 
 // Decoded position (Sec. 3.3): x = min + float(X) * cell per axis, binary32.
 // float(X) and the products of x and y are formed as one packed pair each.
-// The k = 1 shortcut takes Y where it sits: 2^23 + (a & 0xFFC00) - 2^23 is
-// Y * 1024 exactly, and times cell.y * 2^-10 (exact for the batches that take
-// it) it is the same real number as Y * cell.y, so it rounds the same; Z is
-// (a >> 20), since words are below 2^30.
 template <int K>
 __device__ __forceinline__ void decode_point(const DecConst& d, uint32_t a, uint32_t b, uint32_t c,
                                              float& x, float& y, float& z) {
-    if (K == 1) {
-        const f2_t fxy = f2_sub(f2_pack(__uint_as_float(0x4B000000u | (a & 1023u)),
-                                        __uint_as_float(0x4B000000u | (a & 0xFFC00u))),
-                                f2_pack(8388608.0f, 8388608.0f));
-        float sx, sy;
-        f2_unpack(f2_mul(fxy, f2_pack(d.cell[0], d.cell_y1)), sx, sy);
-        x = __fadd_rn(d.mn[0], sx);
-        y = __fadd_rn(d.mn[1], sy);
-        const float fz = __fsub_rn(__uint_as_float((a >> 20) + 0x4B000000u), 8388608.0f);
-        z = __fadd_rn(d.mn[2], __fmul_rn(fz, d.cell[2]));
-        return;
-    }
     uint32_t qx, qy, qz;
     decode_q<K>(a, b, c, qx, qy, qz);
     f2_t fxy;
-    if (prec<K>() <= 2)
+    if (K <= 2)
         fxy = f2_sub(f2_pack(__uint_as_float(0x4B000000u | qx), __uint_as_float(0x4B000000u | qy)),
                      f2_pack(8388608.0f, 8388608.0f));
     else
@@ -774,8 +743,8 @@ __device__ __forceinline__ uint32_t raster_group(const CloudView& c, const ViewC
                                                  const DecConst& d, uint32_t g, uint32_t valid) {
     const uint4 q1 = ld_words<STREAM>(c.w1 + g);
     uint4 q2 = make_uint4(0, 0, 0, 0), q3 = make_uint4(0, 0, 0, 0);
-    if (prec<K>() >= 2) q2 = ld_words<STREAM>(c.w2 + g);
-    if (prec<K>() >= 3) q3 = ld_words<STREAM>(c.w3 + g);
+    if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
+    if (K >= 3) q3 = ld_words<STREAM>(c.w3 + g);
     float x[4], y[4], z[4];
     decode_point<K>(d, q1.x, q2.x, q3.x, x[0], y[0], z[0]);
     decode_point<K>(d, q1.y, q2.y, q3.y, x[1], y[1], z[1]);
@@ -837,8 +806,7 @@ __device__ __forceinline__ uint32_t segment_k(const CloudView& c, const ViewCons
                                               const pc_batch& bt, int k, uint32_t p0, uint32_t p1,
                                               uint32_t lane) {
     const DecConst d = make_dec_const(bt, k);
-    if (k == 1) return k1_shortcut(bt) ? segment<1, STREAM>(c, vc, d, p0, p1, lane)
-                                       : segment<4, STREAM>(c, vc, d, p0, p1, lane);
+    if (k == 1) return segment<1, STREAM>(c, vc, d, p0, p1, lane);
     if (k == 2) return segment<2, STREAM>(c, vc, d, p0, p1, lane);
     return segment<3, STREAM>(c, vc, d, p0, p1, lane);
 }
@@ -1023,8 +991,8 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
         const uint32_t g = base + 4u * q;
         const uint4 q1w = ld_words<false>(c.w1 + g);
         uint4 q2w = make_uint4(0, 0, 0, 0), q3w = make_uint4(0, 0, 0, 0);
-        if (prec<K>() >= 2) q2w = ld_words<false>(c.w2 + g);
-        if (prec<K>() >= 3) q3w = ld_words<false>(c.w3 + g);
+        if (K >= 2) q2w = ld_words<false>(c.w2 + g);
+        if (K >= 3) q3w = ld_words<false>(c.w3 + g);
         const uint4 col = ld_words<false>(c.color + g);
         float x[4], y[4], z[4];
         decode_point<K>(d, q1w.x, q2w.x, q3w.x, x[0], y[0], z[0]);
@@ -1100,8 +1068,7 @@ __device__ __forceinline__ uint32_t shade_segment_k(const CloudView& c, const Vi
                                                     const ShadeBuf& sb, const pc_batch& bt, int k,
                                                     uint32_t p0, uint32_t p1, uint32_t lane) {
     const DecConst d = make_dec_const(bt, k);
-    if (k == 1) return k1_shortcut(bt) ? shade_segment<1, MODE>(c, vc, sb, d, p0, p1, lane)
-                                       : shade_segment<4, MODE>(c, vc, sb, d, p0, p1, lane);
+    if (k == 1) return shade_segment<1, MODE>(c, vc, sb, d, p0, p1, lane);
     if (k == 2) return shade_segment<2, MODE>(c, vc, sb, d, p0, p1, lane);
     return shade_segment<3, MODE>(c, vc, sb, d, p0, p1, lane);
 }
@@ -1277,16 +1244,6 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
     }
 }
 
-// Words of a cloud must be below 2^30 (Listing 2 leaves the top two bits zero);
-// the k = 1 decode relies on it. Sets *bad when one is not.
-__global__ void k_check_words(const uint32_t* w, uint64_t n, uint32_t* bad) {
-    uint32_t found = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        found |= w[i] >> 30;
-    if (__any_sync(FULL, found != 0) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
-}
-
 int g_num_sms = 0;
 
 int num_sms() {
@@ -1379,15 +1336,6 @@ cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_
     e = launch_shade_kernel<0>(c, vt, view_base, s, threads, packed, st);
     *launched = 2;
     return e;
-}
-
-cudaError_t launch_check_words(const uint32_t* w, uint64_t n, uint32_t* bad, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
-    const int threads = 256;
-    uint64_t blocks = (n + threads - 1) / threads;
-    blocks = blocks > (uint64_t)num_sms() * 8 ? (uint64_t)num_sms() * 8 : blocks;
-    k_check_words<<<(unsigned)blocks, threads, 0, st>>>(w, n, bad);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s, cudaStream_t st) {

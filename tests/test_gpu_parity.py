@@ -334,37 +334,3 @@ def test_scan_order_cloud_keep_order(cuda_lib):
             assert_same(vis, img, ovis, enc.color, "scan order")
     finally:
         c.close()
-
-
-def test_k1_decode_paths_and_word_rule(ctx):
-    """At k = 1 the kernels keep Y in place and scale the cell by 2^-10, which
-    is exact unless 0 < size.y < 2^-106; batches on both sides of that limit
-    (and size.y = 0) must render as the oracle does. Uploaded first words at
-    or above 2^30 are refused."""
-    rng = np.random.default_rng(12)
-    sizes_y = [0.0, 2.0 ** -106, 2.0 ** -107, 1e-40, 3.0e-39, 1e-20, 0.75]
-    nb, per = len(sizes_y), 4096
-    n = nb * per
-    b = np.zeros(nb, pcr.BATCH_DTYPE)
-    for i, sy in enumerate(sizes_y):
-        b[i]["min"] = (rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), -2.0 - i)
-        b[i]["size"] = (rng.uniform(0.01, 0.4), sy, rng.uniform(0.01, 0.4))
-        b[i]["first"], b[i]["count"] = i * per, per
-    words = [rng.integers(0, 1 << 30, n, dtype=np.uint32) for _ in range(3)]
-    col = rng.integers(0, 1 << 32, n, dtype=np.uint32)
-    m = S.look_at_perspective((0, 0, 1), (0, 0, -5), (0, 1, 0), 50.0, 1.0, 0.1, 100.0)
-    cloud = ctx.upload_encoded(b, *words, col)
-    enc = O.Encoded(b, *words, col, None)
-    for k in (1, 2):
-        [(vis, img)] = gpu_render(ctx, cloud, [pcr.make_view(m, 96, 96, pcr.PC_VIEW_FORCE_K(k))])
-        ovis, _ = O.render(enc, oracle_view(m, 96, 96, force_k=k))
-        assert_same(vis, img, ovis, col, f"k={k}")
-        # winners from most batches, the tiny ones included
-        won = np.unique((ovis[ovis != O.EMPTY] & np.uint64(0xFFFFFFFF)).astype(np.int64) // per)
-        assert len(won) >= 5 and {1, 2, 3} & set(won.tolist())
-    pcr.pc_release_cloud(ctx.h, cloud)
-    bad = words[0].copy()
-    bad[n // 2] |= np.uint32(1 << 30)
-    with pytest.raises(pcr.PCError) as e:
-        ctx.upload_encoded(b, bad, words[1], words[2], col)
-    assert e.value.status == pcr.PC_EINVAL
