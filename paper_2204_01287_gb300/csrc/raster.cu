@@ -759,12 +759,24 @@ __device__ __forceinline__ uint32_t raster_group(const CloudView& c, const ViewC
 // no bounds checks; the first step of an unaligned range and the last step
 // carry a validity mask. STREAM loads bypass L1 (single view), the multi-view
 // kernel keeps the words in cache for the next view.
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned start and size).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p), "r"(bytes) : "memory");
+}
+
 template <int K, bool STREAM>
 __device__ __forceinline__ uint32_t segment(const CloudView& c, const ViewConst& vc,
                                             const DecConst& d, uint32_t p0, uint32_t p1,
                                             uint32_t lane) {
     uint32_t n_atom = 0;
     uint32_t base = p0 & ~3u;
+    if (lane == 0 && p1 > base) {
+        // the segment's words into L2, so that steps after the first hit L2
+        const uint32_t bytes = ((p1 - base) * 4u + 15u) & ~15u;
+        prefetch_l2(c.w1 + base, bytes);
+        if (K >= 2) prefetch_l2(c.w2 + base, bytes);
+        if (K >= 3) prefetch_l2(c.w3 + base, bytes);
+    }
     if (base != p0 && base < p1) {
         const uint32_t g = base + 4u * lane;
         if (g < p1) {
