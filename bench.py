@@ -330,38 +330,69 @@ def small_configs_bench(args, pcr, torch, ctx):
 
 
 def multiview_bench(args, pcr, torch, ctx, cloud, params):
-    """Sec. 3.7: a stereo pair (2016x2240 per eye) and a bundle of 8 random
-    1080p views of the resident cloud, in one launch vs one launch per view;
-    the images must be identical."""
+    """Sec. 3.7: views rendered in one launch vs one launch per view, with
+    identical images. Over the resident cloud: a stereo pair (2016x2240 per
+    eye) and a bundle of 8 random 1080p views. Over small clouds, where a
+    frame's fixed costs (four launches and their tails) outweigh its points:
+    16 views orbiting 1M points in the unit cube at 512x512, and 16 random
+    1280x720 views of 10M terrain points."""
     import pcsynth
 
-    def timed(views, vpl, reps=5):
+    def timed(cl, views, vpl, reps):
         pcr.pc_set_views_per_launch(ctx.h, vpl)
         fbs = ctx.framebuffers(views)
-        ctx.render(cloud, views, fbs)
+        ctx.render(cl, views, fbs)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
-            ctx.render(cloud, views, fbs)
+            ctx.render(cl, views, fbs)
         e1.record()
         torch.cuda.synchronize()
         imgs = [b.cpu() for _, b in fbs]
         return e0.elapsed_time(e1) / reps, imgs
+
+    def compare(cl, views, reps):
+        ms_multi, a = timed(cl, views, 32, reps)
+        ms_single, b = timed(cl, views, 1, reps)
+        return {"ms_per_view_one_launch": ms_multi / len(views),
+                "ms_per_view_one_view_per_launch": ms_single / len(views),
+                "views_per_s_one_launch": len(views) / (ms_multi / 1e3),
+                "views_per_s_one_view_per_launch": len(views) / (ms_single / 1e3),
+                "speedup": ms_single / ms_multi,
+                "identical_bits": all(bool((x == y).all()) for x, y in zip(a, b))}
 
     out = {}
     stereo = [pcr.make_view(pcsynth.stereo(params, 2016, 2240, e, 6.5), 2016, 2240, pcr.PC_VIEW_CULL)
               for e in (0, 1)]
     bundle = [pcr.make_view(pcsynth.random_view(params, 500 + i, 1920, 1080, seed=args.seed),
                             1920, 1080, pcr.PC_VIEW_CULL) for i in range(8)]
-    for name, views in (("stereo_2x2016x2240", stereo), ("bundle_8x1080p", bundle)):
-        ms_multi, a = timed(views, 32)
-        ms_single, b = timed(views, 1)
-        out[name] = {"ms_per_view_one_launch": ms_multi / len(views),
-                     "ms_per_view_one_view_per_launch": ms_single / len(views),
-                     "speedup": ms_single / ms_multi,
-                     "identical_bits": all(bool((x == y).all()) for x, y in zip(a, b))}
+    out["stereo_2x2016x2240"] = compare(cloud, stereo, 5)
+    out["bundle_8x1080p"] = compare(cloud, bundle, 5)
+
+    xyz, rgba = pcsynth.unit_cube(1_000_000, seed=0)
+    cube = ctx.upload(xyz, rgba)
+    orbit = []
+    for i in range(16):
+        a = 2.0 * np.pi * i / 16
+        eye = (0.5 + 2.2 * np.cos(a), 1.4, 0.5 + 2.2 * np.sin(a))
+        m = pcsynth.look_at_perspective(eye, (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 1.0, 0.1, 100.0)
+        orbit.append(pcr.make_view(m, 512, 512, pcr.PC_VIEW_CULL))
+    out["cube_1m_orbit_16x512"] = compare(cube, orbit, 50)
+    pcr.pc_release_cloud(ctx.h, cube)
+
+    tparams = pcsynth.terrain_params(10000.0)
+    n = 10_000_000
+    xyz = np.empty((n, 3), np.float32)
+    rgba = np.empty(n, np.uint32)
+    pcsynth.terrain(n, tparams, seed=args.seed + 2, out=(xyz, rgba))
+    terr = ctx.upload(xyz, rgba)
+    del xyz, rgba
+    views = [pcr.make_view(pcsynth.random_view(tparams, 700 + i, 1280, 720, seed=args.seed),
+                           1280, 720, pcr.PC_VIEW_CULL) for i in range(16)]
+    out["terrain_10m_bundle_16x720p"] = compare(terr, views, 20)
+    pcr.pc_release_cloud(ctx.h, terr)
     pcr.pc_set_views_per_launch(ctx.h, 32)
     return out
 
