@@ -312,7 +312,9 @@ typedef struct {
  * nviews views, all on `stream` with library-owned framebuffers, and keep the
  * fastest for later pc_render and serving launches on this context (fields set
  * in pc_config override it). Results are identical for every candidate; only
- * the time differs. Synchronous. */
+ * the time differs. Synchronous. Renders and serving groups that other threads
+ * launch on this context meanwhile stay correct but take the candidate being
+ * timed, and their time skews the measurement: tune on an idle context. */
 pc_status pc_autotune(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
                       void* stream, pc_tune_result* out);
 

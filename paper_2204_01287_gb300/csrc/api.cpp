@@ -114,8 +114,7 @@ static uint64_t view_hqs_words(const pc_view& v) {
 
 // The shading sum buffer holds the regions of every view of the largest
 // launch group of a render call.
-pc_status Ctx::ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews) {
-    const uint32_t maxv = views_per_launch();
+pc_status Ctx::ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews, uint32_t maxv) {
     uint64_t need = 0;
     for (uint32_t base = 0; base < nviews; base += maxv) {
         uint64_t group = 0;
@@ -151,8 +150,18 @@ std::shared_ptr<Cloud> Ctx::find_cloud(pc_cloud h) {
     return it == clouds.end() ? nullptr : it->second;
 }
 
+Tune Ctx::tune_for(uint32_t nviews) const {
+    std::lock_guard<std::mutex> g(tune_mu);
+    return tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
+}
+
+void Ctx::set_tune(uint32_t nviews, const Tune& t) {
+    std::lock_guard<std::mutex> g(tune_mu);
+    tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)] = t;
+}
+
 RasterShape Ctx::shape_for(uint32_t nviews) {
-    const Tune& t = tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
+    const Tune t = tune_for(nviews);
     RasterShape r;
     r.threads_per_block = cfg.threads_per_block ? (int)cfg.threads_per_block
                           : t.threads_per_block ? t.threads_per_block : 256;
@@ -168,7 +177,7 @@ RasterShape Ctx::shape_for(uint32_t nviews) {
 // every resident raster warp about four segments. LOD frames draw a small part
 // of their cloud, so they take the smallest size.
 uint32_t Ctx::seg_points_for(uint32_t nviews, const Cloud& cl, const RasterShape& shape) const {
-    const Tune& t = tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
+    const Tune t = tune_for(nviews);
     const uint32_t seg = t.seg_points ? t.seg_points : kSegmentPoints;
     if (cl.is_lod) return kMinSegmentPoints;
     const uint64_t warps = std::max<uint64_t>(1, (uint64_t)shape.blocks * shape.threads_per_block / 32);
@@ -184,9 +193,9 @@ uint32_t Ctx::views_per_launch() const {
 
 // The kernels of one frame: per launch group, clear / cull / raster / resolve.
 pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nviews,
-                            const pc_framebuffer* fbs, cudaStream_t st, Slot* slot) {
+                            const pc_framebuffer* fbs, cudaStream_t st, Slot* slot,
+                            uint32_t maxv, bool timing) {
     const CloudView cv = cl.view();
-    const uint32_t maxv = views_per_launch();
     for (uint32_t base = 0; base < nviews; base += maxv) {
         uint64_t accum_off = 0;
         bool shade = false;
@@ -219,7 +228,7 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
             }
         }
         FrameEvents* fe = nullptr;
-        if (timing_on) {
+        if (timing) {
             std::lock_guard<std::mutex> g(mu);
             frame_events.emplace_back();
             fe = &frame_events.back();
@@ -279,18 +288,20 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
     }
     if (!slot) slot = slot_for(st);
     std::lock_guard<std::mutex> sg(slot->mu);
+    const uint32_t maxv = views_per_launch();   // one value for the whole call
     pc_status rc = ensure_capacity(*slot, cl.n_entries, cl.is_lod ? cl.n_batches : 0);
-    if (rc == PC_OK) rc = ensure_hqs(*slot, views, nviews);
+    if (rc == PC_OK) rc = ensure_hqs(*slot, views, nviews, maxv);
     if (rc != PC_OK) return rc;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
-    const bool graph = (cfg.flags & PC_CFG_GRAPHS) && !timing_on &&
+    const bool timing = timing_on.load();
+    const bool graph = (cfg.flags & PC_CFG_GRAPHS) && !timing &&
                        cs == cudaStreamCaptureStatusNone && st != nullptr;
     if (graph) {
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     }
-    rc = launch_frame(cl, views, nviews, fbs, st, slot);
+    rc = launch_frame(cl, views, nviews, fbs, st, slot, maxv, timing);
     if (graph) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(st, &g);
@@ -299,7 +310,6 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
             return rc;
         }
         if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-        const uint32_t maxv = views_per_launch();
         uint64_t shaded = 0;   // the views with a colour pass change the launch layout
         for (uint32_t v = 0; v < nviews; ++v) shaded |= (uint64_t)(hqs_mode(views[v].flags) != 0);
         const uint64_t key = ((uint64_t)nviews << 8) | maxv | ((uint64_t)cl.is_lod << 40) |

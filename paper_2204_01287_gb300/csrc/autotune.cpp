@@ -85,7 +85,8 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
     std::memset(out, 0, sizeof *out);
 
     // 1. single-view launch shape on views[0]
-    Tune best = ctx.tune[1];
+    const Tune saved = ctx.tune_for(1);
+    Tune best = saved;
     double best_ms = 1e30;
     uint32_t cand = 0;
     pc_status rc = PC_OK;
@@ -94,24 +95,29 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
         const int occ = raster_occupancy(tpb, false);
         for (int bps = std::max(1, occ / 2); bps <= occ && rc == PC_OK; ++bps) {
             for (uint32_t seg : {1024u, 2048u, 4096u}) {
-                ctx.tune[1].threads_per_block = tpb;
-                ctx.tune[1].blocks_per_sm = bps;
-                ctx.tune[1].seg_points = seg;
+                Tune t;
+                t.threads_per_block = tpb;
+                t.blocks_per_sm = bps;
+                t.seg_points = seg;
+                ctx.set_tune(1, t);
                 double ms = 0;
                 rc = time_render(ctx, *cl, views, 1, fbs.data(), st, slot, 3, ms);
                 if (rc != PC_OK) break;
                 ++cand;
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best = ctx.tune[1];
+                    best = t;
                 }
             }
         }
     }
+    bool shape_chosen = false;
     if (rc == PC_OK) {
+        shape_chosen = true;
         for (uint32_t v = 1; v <= kMaxViewsPerLaunch; ++v) {
-            ctx.tune[v] = best;
-            if (v > 1) ctx.tune[v].blocks_per_sm = 0;   // multi-view kernel: its own occupancy
+            Tune t = best;
+            if (v > 1) t.blocks_per_sm = 0;   // multi-view kernel: its own occupancy
+            ctx.set_tune(v, t);
         }
         out->threads_per_block = (uint32_t)best.threads_per_block;
         out->blocks_per_sm = (uint32_t)best.blocks_per_sm;
@@ -148,7 +154,10 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
     } else {
         ctx.tuned_views_per_launch = saved_vpl;
     }
-    if (rc != PC_OK) ctx.tuned_views_per_launch = saved_vpl;
+    if (rc != PC_OK) {   // keep the previous choices that were not replaced
+        ctx.tuned_views_per_launch = saved_vpl;
+        if (!shape_chosen) ctx.set_tune(1, saved);
+    }
     out->candidates = cand;
     ctx.timing_on = timing;
     return rc != PC_OK ? rc : ctx.check_device_error(*slot);

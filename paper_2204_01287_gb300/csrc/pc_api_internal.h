@@ -81,10 +81,12 @@ struct Ctx {
     pc_cloud next_handle = 0;
     std::mutex err_mu;
     std::string last_error, err_copy;
-    bool timing_on = false;
+    std::atomic<bool> timing_on{false};   // read once per pc_render call
     std::deque<FrameEvents> frame_events;
     std::atomic<uint64_t> launches{0};
     std::atomic<uint64_t> raster_launches{0};
+    mutable std::mutex tune_mu;             // guards tune[]: pc_autotune writes it while
+                                            // serving threads may be launching
     Tune tune[kMaxViewsPerLaunch + 1];      // autotuner results by views per launch
     std::atomic<uint32_t> tuned_views_per_launch{0};   // 0: cfg.max_views_per_launch
     ServeState* serve = nullptr;
@@ -95,12 +97,15 @@ struct Ctx {
     Slot* slot_for(cudaStream_t st);
     std::shared_ptr<Cloud> find_cloud(pc_cloud h);
     pc_status ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes);
-    pc_status ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews);
+    pc_status ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews, uint32_t maxv);
     RasterShape shape_for(uint32_t nviews);
     uint32_t seg_points_for(uint32_t nviews, const Cloud& cl, const RasterShape& shape) const;
     uint32_t views_per_launch() const;
+    Tune tune_for(uint32_t nviews) const;
+    void set_tune(uint32_t nviews, const Tune& t);
     pc_status launch_frame(const Cloud& cl, const pc_view* views, uint32_t nviews,
-                           const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);
+                           const pc_framebuffer* fbs, cudaStream_t st, Slot* slot, uint32_t maxv,
+                           bool timing);
     pc_status render(const Cloud& cl, const pc_view* views, uint32_t nviews,
                      const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);
     pc_status check_device_error(Slot& s);
