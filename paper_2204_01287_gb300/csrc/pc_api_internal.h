@@ -89,7 +89,7 @@ struct Ctx {
                                             // serving threads may be launching
     Tune tune[kMaxViewsPerLaunch + 1];      // autotuner results by views per launch
     std::atomic<uint32_t> tuned_views_per_launch{0};   // 0: cfg.max_views_per_launch
-    ServeState* serve = nullptr;
+    std::atomic<ServeState*> serve{nullptr};   // set once, by the first pc_submit
 
     void fail_msg(const char* fmt, ...);
     pc_status cuda_fail(cudaError_t e, const char* what);

@@ -337,7 +337,7 @@ pc_status pc_submit(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nv
             if (rc != PC_OK) return rc;
         }
     }
-    ServeState& s = *ctx->serve;
+    ServeState& s = *ctx->serve.load();
     auto r = std::make_unique<Request>();
     r->cloud = cl;
     r->views.assign(views, views + nviews);
@@ -345,8 +345,10 @@ pc_status pc_submit(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nv
     r->host.resize(nviews);
     for (uint32_t v = 0; v < nviews; ++v) {
         const pc_view& pv = views[v];
-        if (pv.width == 0 || pv.height == 0 || pv.width > kMaxDim || pv.height > kMaxDim)
+        if (pv.width == 0 || pv.height == 0 || pv.width > kMaxDim || pv.height > kMaxDim) {
+            ctx->fail_msg("view %u: size %ux%u outside 1..%u", v, pv.width, pv.height, kMaxDim);
             return PC_EINVAL;
+        }
         if (fbs && (!fbs[v].vis || ((uintptr_t)fbs[v].vis & 15) || ((uintptr_t)fbs[v].rgba & 15))) {
             ctx->fail_msg("view %u: framebuffer missing or not 16-byte aligned", v);
             return PC_EINVAL;
@@ -398,8 +400,9 @@ pc_status pc_submit(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nv
 pc_status pc_poll(pc_ctx* h, pc_ticket ticket, int32_t timeout_ms, pc_result* out) {
     if (!h || !out) return PC_EINVAL;
     Ctx* ctx = reinterpret_cast<Ctx*>(h);
-    if (!ctx->serve) return PC_ENOTFOUND;
-    ServeState& s = *ctx->serve;
+    ServeState* sp = ctx->serve.load();
+    if (!sp) return PC_ENOTFOUND;
+    ServeState& s = *sp;
     std::unique_lock<std::mutex> lk(s.mu);
     auto it = s.reqs.find(ticket);
     if (it == s.reqs.end()) return PC_ENOTFOUND;
@@ -426,8 +429,9 @@ pc_status pc_poll(pc_ctx* h, pc_ticket ticket, int32_t timeout_ms, pc_result* ou
 pc_status pc_release_ticket(pc_ctx* h, pc_ticket ticket) {
     if (!h) return PC_EINVAL;
     Ctx* ctx = reinterpret_cast<Ctx*>(h);
-    if (!ctx->serve) return PC_ENOTFOUND;
-    ServeState& s = *ctx->serve;
+    ServeState* sp = ctx->serve.load();
+    if (!sp) return PC_ENOTFOUND;
+    ServeState& s = *sp;
     std::unique_ptr<Request> gone;
     {
         std::lock_guard<std::mutex> g(s.mu);
