@@ -116,8 +116,9 @@ const char* pc_last_error(pc_ctx* ctx);
  * Eq. 1's 30-bit coordinates split into three words per point. Outputs (host,
  * caller-allocated): batches[ceil(n / batch_size)], w1/w2/w3/color[n] in sorted
  * order, perm[n] (sorted position -> input index; may be NULL). rgba may be NULL
- * (colour 0). threads = 0 uses all cores. PC_EINVAL if n >= 2^32 or batch_size
- * is 0 or not a multiple of 4. */
+ * (colour 0). threads = 0 uses all cores. PC_EINVAL if n >= 2^32, batch_size
+ * is 0 or not a multiple of 4, or a coordinate is a NaN or an infinity (Eq. 1
+ * needs finite boxes). */
 pc_status pc_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
                     uint32_t batch_size, uint32_t threads, uint32_t flags, pc_batch* batches,
                     uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color,
@@ -171,7 +172,9 @@ typedef struct {
  * point lives in one node). Each node is a batch on its cube, quantized with
  * Eq. 1 against it. Rendering a LOD cloud draws a node when it is in the
  * frustum, its projected extent is >= the view's lod_px (the root needs only
- * the frustum) and its parent is drawn. *out receives a new cloud; src stays. */
+ * the frustum) and its parent is drawn. *out receives a new cloud; src stays.
+ * The host holds copies of the cloud and the tree while it builds (up to 56
+ * bytes per point); PC_ENOMEM when they do not fit. */
 pc_status pc_build_lod(pc_ctx* ctx, pc_cloud src, const pc_lod_opts* opts, pc_cloud* out);
 
 /* Host LOD builder alone (no GPU needed): the tree pc_build_lod uploads, from
@@ -180,7 +183,8 @@ pc_status pc_build_lod(pc_ctx* ctx, pc_cloud src, const pc_lod_opts* opts, pc_cl
  * breadth-first order), parent[] (root: 0) and level[] per node, and per LOD
  * point perm (input index), w1/w2/w3 (Eq. 1 against the node cube) and color,
  * n entries each (every input point lands in exactly one node). *n_nodes gets
- * the node count; PC_ENOMEM when it exceeds max_nodes (n always suffices). */
+ * the node count; PC_ENOMEM when it exceeds max_nodes (n always suffices).
+ * PC_EINVAL if a coordinate is a NaN or an infinity. */
 pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
                         const pc_lod_opts* opts, uint32_t threads, uint64_t max_nodes,
                         pc_batch* nodes, uint32_t* parent, uint32_t* level, uint64_t* n_nodes,

@@ -10,6 +10,7 @@
 // 4. Batches of batch_size consecutive sorted points, binary32 box per batch
 //    (size = max - min), Eq. 1 in binary64 per axis, and the 30-bit values
 //    split into the low / medium / high words (x | y << 10 | z << 20).
+// Coordinates must be finite: a NaN or an infinity is refused with PC_EINVAL.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -197,6 +198,16 @@ void encode_batches(const float* xyz, const uint32_t* rgba, uint64_t n, uint32_t
 
 }  // namespace
 
+bool coords_finite(const float* xyz, uint64_t n, unsigned threads) {
+    std::atomic<bool> ok{true};
+    parallel_for(threads, 3 * n, [&](unsigned, uint64_t lo, uint64_t hi) {
+        bool good = true;
+        for (uint64_t i = lo; i < hi; ++i) good &= std::isfinite(xyz[i]);
+        if (!good) ok = false;
+    });
+    return ok;
+}
+
 pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
                       uint32_t batch_size, unsigned threads, bool keep_order, pc_batch* batches,
                       uint32_t* w1, uint32_t* w2, uint32_t* w3, uint32_t* color,
@@ -207,6 +218,7 @@ pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
     if (n == 0) return PC_OK;
     if (threads == 0) threads = hw_threads();
     threads = std::min<unsigned>(threads, 256);
+    if (!coords_finite(xyz, n, threads)) return PC_EINVAL;   // Eq. 1 needs finite boxes
     std::vector<uint32_t> idx;
     if (keep_order) {
         try {

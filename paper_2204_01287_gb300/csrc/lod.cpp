@@ -140,6 +140,7 @@ pc_status lod_encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
     if (n == 0) return PC_OK;
     if (n >= 0xFFFFFFFFull || max_levels == 0 || M == 0) return PC_EINVAL;
     if (threads == 0) threads = hw_threads();
+    if (!coords_finite(xyz, n, threads)) return PC_EINVAL;   // the root cube must be finite
     // root cube
     float lo[3], hi[3];
     for (int a = 0; a < 3; ++a) lo[a] = hi[a] = xyz[a];
@@ -271,14 +272,8 @@ extern "C" pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint6
     return PC_OK;
 }
 
-extern "C" pc_status pc_build_lod(pc_ctx* h, pc_cloud src, const pc_lod_opts* opts,
-                                  pc_cloud* out) {
-    if (!h || !out) return PC_EINVAL;
-    Ctx& ctx = *reinterpret_cast<Ctx*>(h);
-    *out = 0;
-    pc_lod_opts o{12, 10240, 0, 0};
-    if (opts) o = *opts;
-    if (o.max_levels == 0 || o.max_node_points == 0) return PC_EINVAL;
+static pc_status build_lod(pc_ctx* h, Ctx& ctx, pc_cloud src, const pc_lod_opts& o,
+                           pc_cloud* out) {
     auto cl = ctx.find_cloud(src);
     if (!cl) return PC_ENOTFOUND;
     if (cl->is_lod) {
@@ -346,4 +341,20 @@ extern "C" pc_status pc_build_lod(pc_ctx* h, pc_cloud src, const pc_lod_opts* op
     lod->device_bytes += 2 * nn * sizeof(uint32_t);
     *out = ctx.register_cloud(lod);
     return PC_OK;
+}
+
+extern "C" pc_status pc_build_lod(pc_ctx* h, pc_cloud src, const pc_lod_opts* opts,
+                                  pc_cloud* out) {
+    if (!h || !out) return PC_EINVAL;
+    Ctx& ctx = *reinterpret_cast<Ctx*>(h);
+    *out = 0;
+    pc_lod_opts o{12, 10240, 0, 0};
+    if (opts) o = *opts;
+    if (o.max_levels == 0 || o.max_node_points == 0) return PC_EINVAL;
+    try {   // the host copies of the cloud and the tree are a few times its size
+        return build_lod(h, ctx, src, o, out);
+    } catch (const std::exception& e) {
+        ctx.fail_msg("pc_build_lod: %s", e.what());
+        return PC_ENOMEM;
+    }
 }

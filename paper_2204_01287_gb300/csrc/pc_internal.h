@@ -171,5 +171,8 @@ pc_status encode_host(const float* xyz, const uint32_t* rgba, uint64_t n,
                       uint32_t* perm);
 
 unsigned hw_threads();
+// True when all 3n coordinates are finite (no NaN or infinity), checked with
+// `threads` threads.
+bool coords_finite(const float* xyz, uint64_t n, unsigned threads);
 
 }  // namespace pcr

@@ -55,6 +55,21 @@ def test_empty_and_invalid():
         pcr.pc_encode(np.zeros((4, 3), np.float32), None, batch_size=10)   # not a multiple of 4
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+@pytest.mark.parametrize("flags", [0, pcr.PC_ENCODE_KEEP_ORDER])
+def test_non_finite_coordinates_refused(bad, flags):
+    """Eq. 1 divides by a batch box that a NaN or an infinity would make
+    undefined: the encoder and the LOD builder refuse such clouds."""
+    xyz = np.random.default_rng(1).uniform(0, 1, size=(30000, 3)).astype(np.float32)
+    xyz[29999 - 7, 1] = bad                        # one coordinate, late in the input
+    with pytest.raises(pcr.PCError) as e:
+        pcr.pc_encode(xyz, None, batch_size=1024, threads=4, flags=flags)
+    assert e.value.status == pcr.PC_EINVAL
+    with pytest.raises(pcr.PCError) as e:
+        pcr.pc_lod_encode(xyz, None, max_node_points=1000, threads=4)
+    assert e.value.status == pcr.PC_EINVAL
+
+
 @pytest.mark.parametrize("n", [7, 30000, 104000])
 def test_keep_order_matches_oracle(n):
     """Batches of consecutive input points, no Morton sort (Sec. 4.2 baseline)."""
