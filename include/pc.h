@@ -217,7 +217,9 @@ pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
                                               PC_VIEW_HQS; takes precedence */
 
 typedef struct {
-    float    view_proj[16];   /* world -> clip, column-major */
+    float    view_proj[16];   /* world -> clip, column-major; finite (a NaN or an infinity
+                                 gives an unspecified image, never a write outside the
+                                 framebuffers: every pixel index is bounds-checked) */
     uint32_t width, height;   /* 1..16384 */
     uint32_t flags;           /* PC_VIEW_* */
     float    lod_px;          /* LOD clouds: node threshold in px (Sec. 3.5); 0 = all nodes */
