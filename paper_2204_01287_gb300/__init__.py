@@ -4,7 +4,7 @@ Thin ctypes marshalling over the C ABI in include/pc.h; the functions keep the
 C names (pc_create, pc_upload_cloud, pc_render, ...). Every step of a frame runs
 in the library's CUDA kernels; PyTorch only supplies device memory (tensors)
 and streams. There is no CPU fallback: if libpcr.so is missing or fails to
-load, importing the binding raises.
+load, the first call into the library raises.
 
 Convenience layer: :class:`Context` wraps a pc_ctx with numpy/torch helpers.
 """
@@ -214,12 +214,63 @@ def _np_ptr(a):
     return None if a is None else a.ctypes.data
 
 
+# The C ABI takes bare pointers and counts, so the sizes that make its reads
+# and writes stay inside the caller's arrays are checked here.
+
+class _Framebuffers(tuple):
+    """(vis, rgba) tensor pairs made by Context.framebuffers, with the pixel
+    count each pair holds; a tuple, so its tensors cannot be swapped."""
+
+    def __new__(cls, pairs, npix, device):
+        t = super().__new__(cls, pairs)
+        t.npix = tuple(npix)
+        t.device = device
+        return t
+
+    def fits(self, views, device) -> bool:
+        return (device == self.device and len(views) == len(self.npix) and
+                all(int(v.width) * int(v.height) <= n for v, n in zip(views, self.npix)))
+
+
+def _as_xyz(xyz) -> np.ndarray:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    if xyz.ndim != 2 or xyz.shape[1] != 3:
+        raise ValueError(f"xyz must have shape (n, 3), got {xyz.shape}")
+    return xyz
+
+
+def _as_rgba(rgba, n: int):
+    if rgba is None:
+        return None
+    rgba = np.ascontiguousarray(rgba, np.uint32)
+    if rgba.size != n:
+        raise ValueError(f"rgba must hold one colour per point ({n}), got {rgba.size}")
+    return rgba
+
+
+def _check_framebuffers(views, fbs, device: int) -> None:
+    """Each (vis, rgba) torch pair must hold the view's pixels (8 and 4 bytes
+    each) contiguously on the context's CUDA device."""
+    if len(fbs) != len(views):
+        raise ValueError(f"{len(views)} views but {len(fbs)} framebuffers")
+    for i, (v, (vis, rgba)) in enumerate(zip(views, fbs)):
+        npix = int(v.width) * int(v.height)
+        pairs = ((vis, 8, "vis"), (rgba, 4, "rgba"))
+        for t, nb, name in pairs:
+            if t.numel() * t.element_size() < npix * nb or not t.is_contiguous():
+                raise ValueError(f"view {i}: {name} must be a contiguous tensor of at least "
+                                 f"{npix * nb} bytes")
+        for t, _, name in pairs:
+            if t.device.type != "cuda" or t.device.index != device:
+                raise ValueError(f"view {i}: {name} is on {t.device}, the context on cuda:{device}")
+
+
 def pc_encode(xyz: np.ndarray, rgba: np.ndarray | None, batch_size: int = 10240,
               threads: int = 0, flags: int = 0):
     """Host encoder: returns (batches, w1, w2, w3, color, perm) numpy arrays."""
-    xyz = np.ascontiguousarray(xyz, np.float32)
+    xyz = _as_xyz(xyz)
     n = xyz.shape[0]
-    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    rgba = _as_rgba(rgba, n)
     nb = (n + batch_size - 1) // batch_size
     batches = np.zeros(nb, BATCH_DTYPE)
     w = [np.zeros(n, np.uint32) for _ in range(4)]
@@ -231,8 +282,8 @@ def pc_encode(xyz: np.ndarray, rgba: np.ndarray | None, batch_size: int = 10240,
 
 
 def pc_upload_cloud(ctx: int, xyz: np.ndarray, rgba: np.ndarray | None) -> int:
-    xyz = np.ascontiguousarray(xyz, np.float32)
-    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    xyz = _as_xyz(xyz)
+    rgba = _as_rgba(rgba, xyz.shape[0])
     out = ctypes.c_uint64()
     _check(ctx, lib().pc_upload_cloud(ctx, _np_ptr(xyz), _np_ptr(rgba), xyz.shape[0],
                                       ctypes.byref(out)))
@@ -240,7 +291,10 @@ def pc_upload_cloud(ctx: int, xyz: np.ndarray, rgba: np.ndarray | None) -> int:
 
 
 def pc_upload_encoded(ctx: int, batches, w1, w2, w3, color) -> int:
-    arrs = [np.ascontiguousarray(a, np.uint32) for a in (w1, w2, w3, color)]
+    arrs = [np.ascontiguousarray(a, np.uint32).reshape(-1) for a in (w1, w2, w3, color)]
+    if len({len(a) for a in arrs}) != 1:
+        raise ValueError("w1, w2, w3 and color must have one entry per point each, got "
+                         f"{[len(a) for a in arrs]}")
     b = np.ascontiguousarray(batches, BATCH_DTYPE)
     out = ctypes.c_uint64()
     _check(ctx, lib().pc_upload_encoded(ctx, _np_ptr(b), len(b), *(a.ctypes.data for a in arrs),
@@ -278,9 +332,9 @@ def pc_lod_encode(xyz: np.ndarray, rgba, max_levels: int = 12, max_node_points: 
                   seed: int = 0, threads: int = 0, max_nodes: int | None = None):
     """Host LOD builder: (nodes, parent, level, perm, w1, w2, w3, color).
     max_nodes bounds the node arrays (default: one per point)."""
-    xyz = np.ascontiguousarray(xyz, np.float32)
+    xyz = _as_xyz(xyz)
     n = xyz.shape[0]
-    rgba = None if rgba is None else np.ascontiguousarray(rgba, np.uint32)
+    rgba = _as_rgba(rgba, n)
     cap = max(int(max_nodes) if max_nodes else n, 1)
     nodes = np.zeros(cap, BATCH_DTYPE)
     parent = np.zeros(cap, np.uint32)
@@ -324,6 +378,13 @@ def pc_render(ctx: int, cloud: int, views, fbs, stream: int = 0) -> None:
 
 def pc_render_host(ctx: int, cloud: int, views, out_images, stream: int = 0) -> None:
     """out_images: list of writable numpy uint32 arrays (width*height each)."""
+    if len(out_images) != len(views):
+        raise ValueError(f"{len(views)} views but {len(out_images)} images")
+    for i, (v, o) in enumerate(zip(views, out_images)):
+        if (not isinstance(o, np.ndarray) or o.nbytes < 4 * int(v.width) * int(v.height)
+                or not o.flags.c_contiguous or not o.flags.writeable):
+            raise ValueError(f"view {i}: the image must be a writable contiguous array of "
+                             f"{v.width}x{v.height} 32-bit pixels")
     va = _views_arr(views)
     ptrs = (ctypes.c_void_p * len(views))(*[o.ctypes.data for o in out_images])
     _check(ctx, lib().pc_render_host(ctx, cloud, va, len(views), ptrs, stream))
@@ -426,18 +487,25 @@ class Context:
         return pc_upload_encoded(self.h, batches, w1, w2, w3, color)
 
     def framebuffers(self, views):
-        """torch (vis, rgba) tensors for each view, on this device."""
+        """torch (vis, rgba) tensors for each view, on this device: an
+        immutable sequence that remembers the pixel counts it was made for."""
         import torch
         dev = torch.device("cuda", self.device)
-        return [(torch.empty(v.height * v.width, dtype=torch.int64, device=dev),
-                 torch.empty(v.height * v.width, dtype=torch.int32, device=dev)) for v in views]
+        return _Framebuffers(
+            [(torch.empty(v.height * v.width, dtype=torch.int64, device=dev),
+              torch.empty(v.height * v.width, dtype=torch.int32, device=dev)) for v in views],
+            [int(v.width) * int(v.height) for v in views], self.device)
 
     def render(self, cloud, views, fbs=None, stream=None):
         """Render views into torch framebuffers (allocated when fbs is None)
-        on `stream` (a torch.cuda.Stream; default the current stream)."""
+        on `stream` (a torch.cuda.Stream; default the current stream). fbs not
+        made by framebuffers() for views at least this large is checked tensor
+        by tensor (size, contiguity, device) before the launch."""
         import torch
         if fbs is None:
             fbs = self.framebuffers(views)
+        elif not (isinstance(fbs, _Framebuffers) and fbs.fits(views, self.device)):
+            _check_framebuffers(views, fbs, self.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         pc_render(self.h, cloud, views, [(a.data_ptr(), b.data_ptr()) for a, b in fbs],
                   s.cuda_stream)
