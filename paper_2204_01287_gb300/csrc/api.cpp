@@ -78,14 +78,23 @@ Slot::~Slot() {
 }
 
 pc_status Ctx::ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes) {
+    // each buffer on its own, so a failed allocation is retried by the next call
     if (!s.scratch.counters) {
         cudaError_t e = cudaMalloc(&s.scratch.counters, sizeof(uint32_t) * C_COUNT);
-        if (e != cudaSuccess) return cuda_fail(e, "scratch counters");
+        if (e != cudaSuccess) {
+            s.scratch.counters = nullptr;
+            return cuda_fail(e, "scratch counters");
+        }
         cudaMemsetAsync(s.scratch.counters, 0, sizeof(uint32_t) * C_COUNT, s.stream);
-        e = cudaMalloc(&s.scratch.stats, sizeof(unsigned long long) * kMaxViewsPerRender * S_COUNT);
-        if (e != cudaSuccess) return cuda_fail(e, "scratch stats");
-        cudaMemsetAsync(s.scratch.stats, 0,
-                        sizeof(unsigned long long) * kMaxViewsPerRender * S_COUNT, s.stream);
+    }
+    if (!s.scratch.stats) {
+        const size_t bytes = sizeof(unsigned long long) * kMaxViewsPerRender * S_COUNT;
+        cudaError_t e = cudaMalloc(&s.scratch.stats, bytes);
+        if (e != cudaSuccess) {
+            s.scratch.stats = nullptr;
+            return cuda_fail(e, "scratch stats");
+        }
+        cudaMemsetAsync(s.scratch.stats, 0, bytes, s.stream);
     }
     if (entries > s.scratch.capacity) {
         cudaStreamSynchronize(s.stream);
