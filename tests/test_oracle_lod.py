@@ -207,3 +207,99 @@ def test_foveated_selection(lod):
             e = O.projected_extent(t.nodes[i], v)
             if e is not None:
                 assert e >= 100.0
+
+
+# ---- rules pinned on hand-made inputs ----------------------------------------------
+
+def _boxes(boxes, parents):
+    """A node list from (min, size) boxes, for selection only."""
+    nodes = np.zeros(len(boxes), O.BATCH_DTYPE)
+    for i, (lo, size) in enumerate(boxes):
+        nodes[i]["min"], nodes[i]["size"] = lo, size
+    return O.LodCloud(nodes, np.asarray(parents, np.uint32), np.zeros(len(boxes), np.uint32),
+                      None, None, None, None, None)
+
+
+# identity view of 100x100 pixels: w = 1 everywhere and pixel f = 50 x + 50, so a
+# box of side s in x and y projects to 50 s pixels around 50 + 50 x_centre
+IDENTITY = np.eye(4, dtype=np.float32)
+
+
+def test_selection_root_and_parent_rules():
+    """The root needs only the frustum (even when tiny); any other node also
+    needs its parent drawn, even when it is in view and large itself."""
+    v = O.make_view(IDENTITY, 100, 100)
+    t = _boxes([((-0.01, -0.01, 0), (0.02, 0.02, 0)),     # 0: root, 1 px
+                ((2.0, 2.0, 0), (1.0, 1.0, 0)),           # 1: outside the frustum
+                ((-0.5, -0.5, 0), (1.0, 1.0, 0)),         # 2: 50 px, parent culled
+                ((-0.5, -0.5, 0), (1.0, 1.0, 0))],        # 3: 50 px, parent the root
+               [0, 0, 1, 0])
+    assert O.cull(t.nodes[1], v) and not O.cull(t.nodes[2], v)
+    assert list(O.lod_select(t, v, 10.0)) == [1, 0, 0, 1]
+
+
+def test_foveated_threshold_by_ring():
+    """lod_px = 10 in ring 0, (10 + 30) / 2 = 20 in ring 1, 30 in ring 2 (the
+    ring of the projected box's centre; 100x100: R2 = 5000, ring 0 iff
+    9 d2 < 5000, ring 1 iff 9 d2 < 20000). Centres: (85, 50) is d = 35, ring 1;
+    (95, 95) is d2 = 4050, ring 2; (50, 50) is ring 0."""
+    v = O.make_view(IDENTITY, 100, 100)
+    t = _boxes([((-1, -1, 0), (2, 2, 0)),                 # root
+                ((0.55, -0.15, 0), (0.3, 0.3, 0)),        # ring 1, 15 px: below 20
+                ((0.45, -0.25, 0), (0.5, 0.5, 0)),        # ring 1, 25 px
+                ((0.7, 0.7, 0), (0.4, 0.4, 0)),           # ring 2, 20 px: below 30
+                ((0.55, 0.55, 0), (0.7, 0.7, 0)),         # ring 2, 35 px
+                ((-0.12, -0.12, 0), (0.24, 0.24, 0)),     # ring 0, 12 px
+                ((-0.08, -0.08, 0), (0.16, 0.16, 0))],    # ring 0, 8 px: below 10
+               [0] * 7)
+    assert [O.ring(85, 50, 100, 100), O.ring(95, 95, 100, 100)] == [1, 2]
+    assert list(O.lod_select(t, v, 10.0, 30.0)) == [1, 0, 1, 0, 1, 1, 0]
+    assert list(O.lod_select(t, v, 10.0)) == [1, 1, 1, 1, 1, 1, 0]
+
+
+def test_root_is_the_cubic_box():
+    """Corner = per-axis minimum, side = the largest extent (here y's)."""
+    rng = np.random.default_rng(3)
+    xyz = (rng.random((50, 3)) * [1.0, 3.0, 2.0] + [5.0, -1.0, 2.0]).astype(np.float32)
+    xyz[0] = (5.0, -1.0, 2.0)
+    xyz[1] = (6.0, 2.0, 4.0)
+    t = O.lod_build(xyz, np.zeros(50, np.uint32), L, 1000, SEED)
+    assert len(t.nodes) == 1
+    assert list(t.nodes[0]["min"]) == [5.0, -1.0, 2.0]
+    assert list(t.nodes[0]["size"]) == [3.0, 3.0, 3.0]
+
+
+def test_split_only_above_max_node_points():
+    rng = np.random.default_rng(4)
+    xyz = rng.random((101, 3)).astype(np.float32)
+    rgba = np.zeros(101, np.uint32)
+    assert len(O.lod_build(xyz[:100], rgba[:100], L, 100, SEED).nodes) == 1   # exactly M: a leaf
+    t = O.lod_build(xyz, rgba, L, 100, SEED)
+    assert len(t.nodes) == 2 and list(t.nodes["count"]) == [100, 1]
+
+
+def test_depth_limit_keeps_every_point_in_the_last_level():
+    """max_levels = 2: the root splits, its children are at the last level and
+    keep all their points however many."""
+    rng = np.random.default_rng(5)
+    xyz = rng.random((5000, 3)).astype(np.float32)
+    t = O.lod_build(xyz, np.zeros(5000, np.uint32), 2, 100, SEED)
+    assert int(t.level.max()) == 1 and len(t.nodes) == 9
+    assert t.nodes["count"][0] == 100 and t.nodes["count"][1:].min() > 100
+    assert t.nodes["count"].sum() == 5000
+
+
+def test_dilation_window_is_set_by_the_pixel_centre_ring():
+    """One point at q shows in pixel p exactly when q is within Chebyshev
+    distance 1 + ring(p's centre) of p: a sweep of q across the ring
+    boundaries of a 64x64 view."""
+    W = H = 64
+    color = np.array([0x5A], np.uint32)
+    py, px = np.mgrid[0:H, 0:W]
+    radius = np.array([[1 + O.ring(x + 0.5, y + 0.5, W, H) for x in range(W)] for y in range(H)])
+    for qx, qy in [(x, 32) for x in range(0, 64, 3)] + [(x, x) for x in range(1, 64, 4)]:
+        vis = np.full(W * H, O.EMPTY, np.uint64)
+        vis[qy * W + qx] = (7 << 32) | 0
+        out = O.resolve_dilated(vis, W, H, color).reshape(H, W)
+        reach = np.maximum(abs(px - qx), abs(py - qy)) <= radius
+        assert np.array_equal(out == 0x5A, reach), (qx, qy)

@@ -2,8 +2,8 @@
 
 Each case copies oracle/pcr_oracle.c into a temporary directory, plants one
 plausible mistake (a dropped term, a wrong sign, shift or index, a transposed
-operand, a wrong tie-break), builds the copy and runs tests/test_oracle_pins.py
-against it. Every planted mistake must make at least one pin fail. The oracle
+operand, a wrong tie-break), builds the copy and runs the pins of that part of
+the oracle against it. Every planted mistake must make at least one pin fail. The oracle
 in the tree is never modified.
 """
 import os
@@ -83,9 +83,53 @@ VERIFY_MUTANTS = [
     ("verify_lod_no_order", "(i > B->first && idx <= prev)", "(0)"),
 ]
 
+# Sec. 3.5 level of detail and Sec. 3.7 foveation and dilation, checked by the
+# pins of tests/test_oracle_lod.py
+LOD_MUTANTS = [
+    ("lod_root_not_cubic", "        if (e > side) side = e;\n    }\n    /* breadth-first",
+     "        if (a == 0) side = e;\n    }\n    /* breadth-first"),
+    ("lod_priority_seed", "pr[j].pri = or_splitmix64(((uint64_t)seed << 32) + w.idx[j]);",
+     "pr[j].pri = or_splitmix64(((uint64_t)seed << 16) + w.idx[j]);"),
+    ("lod_keep_largest", "if (x->pri != y->pri) return x->pri < y->pri ? -1 : 1;",
+     "if (x->pri != y->pri) return x->pri > y->pri ? -1 : 1;"),
+    ("lod_depth_limit", "if (w.n > max_node_points && w.level + 1 < max_levels) {",
+     "if (w.n > max_node_points && w.level < max_levels) {"),
+    ("lod_mid_quarter", "for (int a = 0; a < 3; ++a) mid[a] = w.lo[a] + half;",
+     "for (int a = 0; a < 3; ++a) mid[a] = w.lo[a] + half * 0.5f;"),
+    ("lod_child_corner", "for (int a = 0; a < 3; ++a) c->lo[a] = ((o >> a) & 1) ? mid[a] : w.lo[a];",
+     "for (int a = 0; a < 3; ++a) c->lo[a] = ((o >> a) & 1) ? w.lo[a] + w.size : w.lo[a];"),
+    ("lod_child_size", "c->size = half;", "c->size = w.size;"),
+    ("lod_kept_priority_order", "qsort(kept, keep, sizeof(uint32_t), u32_cmp);   /* input order */",
+     "/* kept in priority order */"),
+    ("lod_select_no_parent", "if (ok && i > 0) ok = sel[parent[i]];", "if (0) ok = sel[parent[i]];"),
+    ("lod_select_root_extent", "        int ok = !or_cull(&nodes[i], v);\n        if (ok && i > 0) {",
+     "        int ok = !or_cull(&nodes[i], v);\n        if (ok) {"),
+    ("lod_select_no_cull", "        int ok = !or_cull(&nodes[i], v);", "        int ok = 1;"),
+    ("ring0_wider", "if (9.0f * d2 < r2) return 0;", "if (4.0f * d2 < r2) return 0;"),
+    ("ring1_threshold", "if (ring == 1) t = (lod_px + lod_px_periphery) * 0.5f;",
+     "if (ring == 1) t = lod_px;"),
+    ("ring2_threshold", "if (ring == 2) t = lod_px_periphery;", "if (ring == 2) t = lod_px;"),
+    ("dilate_radius",
+     "            int r = 1 + or_ring((float)px + 0.5f, (float)py + 0.5f, width, height);\n"
+     "            uint64_t best = OR_EMPTY;",
+     "            int r = or_ring((float)px + 0.5f, (float)py + 0.5f, width, height);\n"
+     "            uint64_t best = OR_EMPTY;"),
+    ("dilate_ring_at_corner",
+     "            int r = 1 + or_ring((float)px + 0.5f, (float)py + 0.5f, width, height);\n"
+     "            uint64_t best = OR_EMPTY;",
+     "            int r = 1 + or_ring((float)px, (float)py, width, height);\n"
+     "            uint64_t best = OR_EMPTY;"),
+    ("dilate_farthest",
+     "                    uint64_t k = vis[(uint64_t)y * width + (uint64_t)x];\n"
+     "                    if (k < best) best = k;",
+     "                    uint64_t k = vis[(uint64_t)y * width + (uint64_t)x];\n"
+     "                    if (k != OR_EMPTY && (best == OR_EMPTY || k > best)) best = k;"),
+]
+
 CASES = ([m + ("test_oracle_pins.py",) for m in MUTANTS] +
          [m + ("test_oracle_hqs.py",) for m in HQS_MUTANTS] +
-         [m + ("test_oracle_verify.py",) for m in VERIFY_MUTANTS])
+         [m + ("test_oracle_verify.py",) for m in VERIFY_MUTANTS] +
+         [m + ("test_oracle_lod.py",) for m in LOD_MUTANTS])
 
 
 @pytest.mark.parametrize("name,old,new,pins", CASES, ids=[m[0] for m in CASES])
