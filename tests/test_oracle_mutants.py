@@ -47,6 +47,42 @@ MUTANTS = [
      "if (jobs[t].vis[p] > vis[p] && jobs[t].vis[p] != OR_EMPTY) vis[p] = jobs[t].vis[p];"),
     ("index_not_global", "uint32_t i = b->first + j;\n            uint32_t pix;",
      "uint32_t i = j;\n            uint32_t pix;"),
+    # per-frame counters (Table 2), their threaded merge, clamps, the culling
+    # rounding bound, the resolve background, the view's rows and columns
+    ("stats_points_k_one",
+     "            st->points_k[k] += b->count;\n        }\n        for (uint32_t j = 0; j < b->count; ++j) {\n            uint32_t i = b->first + j;",
+     "            st->points_k[k] += 1;\n        }\n        for (uint32_t j = 0; j < b->count; ++j) {\n            uint32_t i = b->first + j;"),
+    ("stats_batches_k_fixed",
+     "            st->batches_k[k] += 1;\n            st->points_k[k] += b->count;\n        }\n        for (uint32_t j = 0; j < b->count; ++j) {\n            uint32_t i = b->first + j;",
+     "            st->batches_k[1] += 1;\n            st->points_k[k] += b->count;\n        }\n        for (uint32_t j = 0; j < b->count; ++j) {\n            uint32_t i = b->first + j;"),
+    ("stats_accepted_all",
+     "            if (!or_project_point(b, k, w1[i], w2[i], w3[i], i, v, &pix, &key)) continue;\n            if (st) st->points_accepted += 1;",
+     "            if (st) st->points_accepted += 1;\n            if (!or_project_point(b, k, w1[i], w2[i], w3[i], i, v, &pix, &key)) continue;"),
+    ("threaded_merge_drops_k", "                st->points_k[k] += jobs[t].st.points_k[k];",
+     "                st->points_k[k] = jobs[t].st.points_k[k];"),
+    ("threaded_merge_drops_batches", "            st->batches_rendered += jobs[t].st.batches_rendered;",
+     "            st->batches_rendered = jobs[t].st.batches_rendered;"),
+    ("morton_scale", "if (csize[a] > 0.0) t = floor(2097152.0 *", "if (csize[a] > 0.0) t = floor(1048576.0 *"),
+    ("morton_no_clamp", "if (t > 2097151.0) t = 2097151.0;", ";"),
+    ("eq1_no_clamp", "if (t > 1073741823.0) t = 1073741823.0;", ";"),
+    ("cull_no_rounding_bound", "const double g = 6.0 * 0x1.0p-24;", "const double g = 0.0;"),
+    ("cull_wide_margin", "const double e1 = 1.0 + 0x1.0p-10;", "const double e1 = 1.5;"),
+    ("resolve_background", "out[p] = vis[p] == OR_EMPTY ? 0u : color",
+     "out[p] = vis[p] == OR_EMPTY ? 0xFF000000u : color"),
+    ("project_no_m12", "float cx = ((m[0] * x + m[4] * y) + m[8] * z) + m[12];",
+     "float cx = ((m[0] * x + m[4] * y) + m[8] * z);"),
+    ("pixel_width_for_y", "float fy = (ndy * 0.5f + 0.5f) * (float)v->height;",
+     "float fy = (ndy * 0.5f + 0.5f) * (float)v->width;"),
+    ("pixel_row_stride", "*pixel = py * v->width + px;", "*pixel = py * v->height + px;"),
+    ("accept_right_edge", "if (!(fx >= 0.0f && fx < (float)v->width)) return 0;",
+     "if (!(fx >= 0.0f && fx <= (float)v->width)) return 0;"),
+    ("select_k_behind_1", "        if (!(cw > 0.0f)) return 3;\n        float f[2];",
+     "        if (!(cw > 0.0f)) return 1;\n        float f[2];"),
+    ("select_k_threshold_le", "if (ex < T && ey < T) return 1;", "if (ex <= T && ey <= T) return 1;"),
+    ("decode_half_cell", "float off = fq * cell;", "float off = fq * cell * 0.5f;"),
+    ("in_order_box_min_from_first",
+     "                if (v < bmin[a]) bmin[a] = v;\n                if (v > bmax[a]) bmax[a] = v;\n            }\n        or_batch* B = &batches[b];\n        for (int a = 0; a < 3; ++a) {\n            B->min[a] = bmin[a];\n            B->size[a] = bmax[a] - bmin[a];\n        }\n        B->first = (uint32_t)first;",
+     "                if (v > bmax[a]) bmax[a] = v;\n            }\n        or_batch* B = &batches[b];\n        for (int a = 0; a < 3; ++a) {\n            B->min[a] = bmin[a];\n            B->size[a] = bmax[a] - bmin[a];\n        }\n        B->first = (uint32_t)first;"),
 ]
 
 # Sec. 3.6 high-quality shading, checked by the pins of tests/test_oracle_hqs.py

@@ -335,11 +335,13 @@ def _ortho(scale=1.0):
 
 @pytest.mark.parametrize("s,T,want", [(0.99, 512.0, 1), (1.01, 512.0, 2),
                                       (0.99, 500.0, 2), (0.97, 500.0, 1),
-                                      (1023.0, 512.0, 2), (1025.0, 512.0, 3)])
+                                      (1023.0, 512.0, 2), (1025.0, 512.0, 3),
+                                      (1.0, 512.0, 2), (1024.0, 512.0, 3)])
 def test_select_k_thresholds(s, T, want):
     """Orthographic camera (c = x, w = 1) on a 1024 px wide view: a box of
     width s in x projects to an extent of s * 0.5 * 1024 px (hand-computed:
-    506.88, 517.12, 496.64, 523776, 524800)."""
+    506.88, 517.12, 496.64, 523776, 524800, and exactly 512 and 524288, where
+    the strict comparison of Sec. 3.3's threshold picks the larger k)."""
     b = np.zeros(1, O.BATCH_DTYPE)[0]
     b["min"] = (-s / 2, 0.0, 0.0)
     b["size"] = (s, 0.001, 0.001)
@@ -443,3 +445,99 @@ def test_resolve():
     color = np.array([7, 8, 9, 10], np.uint32)
     vis = np.array([O.EMPTY, (5 << 32) | 2, (1 << 32) | 0, O.EMPTY, (3 << 32) | 3], np.uint64)
     assert list(O.resolve(vis, color)) == [0, 9, 7, 0, 10]
+
+
+# ---- per-frame counters (Table 2) on a hand-built cloud ------------------------------
+
+def _hand_stats_cloud():
+    """Four batches under the orthographic camera (c = x, w = 1) of a 64x64
+    view, where f = 32 x + 32 and a point is inside iff -1 <= x, y < 1:
+      A  x in [-0.5, 0], 16 px wide: k = 1, 4 points, all inside;
+      B  x in [-20, 20], 1280 px: k = 2, x = -20, -10, 0, 10, 20: one inside;
+      C  x in [5, 6], right of the view: culled, 3 points;
+      D  x in [-20000, 20000], 1,280,000 px: k = 3, x = -20000 + 10000 j: one inside.
+    Every coordinate is a dyadic grid point of its box, so it decodes exactly
+    at its batch's k."""
+    boxes = [((-0.5, -0.5, 0.0), (0.5, 0.5, 0.0), [(-0.5 + 0.125 * i, -0.5, 0.0) for i in range(4)]),
+             ((-20.0, -0.25, 0.0), (40.0, 0.5, 0.0), [(-20.0 + 10.0 * j, -0.25, 0.0) for j in range(5)]),
+             ((5.0, 0.0, 0.0), (1.0, 0.0, 0.0), [(5.0, 0.0, 0.0), (5.5, 0.0, 0.0), (6.0, 0.0, 0.0)]),
+             ((-20000.0, 0.0, 0.0), (40000.0, 0.0, 0.0),
+              [(-20000.0 + 10000.0 * j, 0.0, 0.0) for j in range(5)])]
+    batches = np.zeros(len(boxes), O.BATCH_DTYPE)
+    words, first = [], 0
+    for i, (mn, sz, pts) in enumerate(boxes):
+        batches[i]["min"], batches[i]["size"] = mn, sz
+        batches[i]["first"], batches[i]["count"] = first, len(pts)
+        first += len(pts)
+        for p in pts:
+            words.append(O.split_words(*[O.quantize30(p[a], mn[a], sz[a]) for a in range(3)]))
+    w = np.array(words, np.uint32)
+    n = len(w)
+    return O.Encoded(batches, w[:, 0].copy(), w[:, 1].copy(), w[:, 2].copy(),
+                     np.arange(n, dtype=np.uint32), np.arange(n, dtype=np.uint32))
+
+
+def test_frame_counters_hand_built():
+    enc = _hand_stats_cloud()
+    m = _ortho()
+    on = O.make_view(m, 64, 64, cull=True)
+    off = O.make_view(m, 64, 64, cull=False)
+    assert [O.select_k(b, on) for b in enc.batches] == [1, 2, 1, 3]
+    want_on = {"batches_rendered": 3, "points_processed": 14, "batches_k": [0, 1, 1, 1],
+               "points_k": [0, 4, 5, 5], "points_accepted": 6}
+    want_off = {"batches_rendered": 4, "points_processed": 17, "batches_k": [0, 2, 1, 1],
+                "points_k": [0, 7, 5, 5], "points_accepted": 6}
+    for v, want in ((on, want_on), (off, want_off)):
+        vis, st = O.render(enc, v)
+        assert {k: st[k] for k in want} == want
+        assert int((vis != O.EMPTY).sum()) == 6
+        for t in (1, 2, 3, 4):          # the threaded merge adds every counter
+            tvis, tst = O.render_threaded(enc, v, threads=t)
+            assert np.array_equal(tvis, vis) and {k: tst[k] for k in want} == want
+
+
+# ---- Sec. 3.2 culling under binary32 rounding -----------------------------------------
+
+def test_culling_covers_binary32_rounding():
+    """One point whose exact clip x is 0.75 % left of -w, but whose binary32
+    row value fl(fl(m0 x) + m12) rounds to exactly -1 = -w, so it lands on
+    pixel column 0 (found by a search, checked here with exact rationals).
+    Culling must keep its batch: the rounding bound of the test, not the
+    plane margin 1 + 2^-10, is what covers it."""
+    from fractions import Fraction
+    m0, x, m12 = 1.5094573497772217, 88018.546875, -132861.25
+    assert np.float32(m0) == m0 and np.float32(x) == x and np.float32(m12) == m12
+    exact = Fraction(m0) * Fraction(x) + Fraction(m12)
+    assert exact < -(1 + Fraction(1, 1024))
+    m = np.zeros(16, np.float32)
+    m[0], m[12], m[5], m[15] = m0, m12, 1.0, 1.0
+    v = O.make_view(m, 64, 64, cull=True)
+    ok, pix, _, fx, _ = O.project_position((x, 0.0, 0.0), v)
+    assert ok and fx == 0.0 and pix == 32 * 64
+    b = np.zeros(1, O.BATCH_DTYPE)[0]
+    b["min"], b["size"], b["count"] = (x, 0.0, 0.0), (0.0, 0.0, 0.0), 1
+    assert not O.cull(b, v)
+
+
+# ---- Sec. 4.2 batches in input order ----------------------------------------------------
+
+def test_encode_in_order_hand_cloud():
+    """Batches of 3 consecutive input points in input order; each box is the
+    per-axis min and max of its own points (none of them the first point's),
+    and the words are Eq. 1 against that box."""
+    pts = [(4, 1, 2), (0, 3, 1), (2, 0, 0),       # box min (0,0,0), size (4,3,2)
+           (1, 5, 7), (-1, 6, 5), (0, 5, 6),      # box min (-1,5,5), size (2,1,2)
+           (9, 9, 9)]                             # a box of size 0
+    xyz = np.array(pts, np.float32)
+    rgba = np.arange(7, dtype=np.uint32) + 50
+    enc = O.encode_in_order(xyz, rgba, batch_size=3)
+    assert [list(b["min"]) for b in enc.batches] == [[0, 0, 0], [-1, 5, 5], [9, 9, 9]]
+    assert [list(b["size"]) for b in enc.batches] == [[4, 3, 2], [2, 1, 2], [0, 0, 0]]
+    assert [int(b["first"]) for b in enc.batches] == [0, 3, 6]
+    assert [int(b["count"]) for b in enc.batches] == [3, 3, 1]
+    assert list(enc.color) == list(rgba)
+    # (0, 3, 1) in the first box: X = 0, Y clamps to 2^30 - 1, Z = 2^29
+    assert O.split_words(0, (1 << 30) - 1, 1 << 29) == [int(enc.w1[1]), int(enc.w2[1]), int(enc.w3[1])]
+    # (-1, 6, 5) in the second box: X = 0, Y = 2^30 - 1, Z = 0
+    assert O.split_words(0, (1 << 30) - 1, 0) == [int(enc.w1[4]), int(enc.w2[4]), int(enc.w3[4])]
+    assert [int(enc.w1[6]), int(enc.w2[6]), int(enc.w3[6])] == [0, 0, 0]
