@@ -131,6 +131,11 @@ def test_dilated_takes_the_winning_pixels_average():
     assert O.ring(4.5, 0.5, W, H) >= 1
     r = 1 + O.ring(4.5, 0.5, W, H)
     assert out[0 * W + 4] == (0xFF010203 if r >= 3 else (0xFF0A0B0C if r >= 2 else 0))
+    # the same two pixels with the keys swapped: now the winner comes first in
+    # the window's row order, and the centre shows its own average
+    vis[3 * W + 1], vis[2 * W + 2] = np.uint64(9 << 32 | 7), np.uint64(5 << 32 | 1)
+    out = O.hqs_resolve_dilated(vis, W, H, hqs)
+    assert out[2 * W + 2] == 0xFF0A0B0C and out[3 * W + 1] == 0xFF0A0B0C
 
 
 def test_lod_hqs_matches_its_geometry_pass():

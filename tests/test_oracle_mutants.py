@@ -98,6 +98,36 @@ HQS_MUTANTS = [
      "const or_batch* B = &nodes[i];\n        int k = or_select_k(B, v);\n        for"),
     ("hqs_dilate_own_pixel", "best == OR_EMPTY ? 0u : hqs[at];",
      "best == OR_EMPTY ? 0u : hqs[(uint64_t)py * width + px];"),
+    ("hqs_alpha_not_255", "((uint32_t)(sum[4 * p + 2] / n) << 16) | (255u << 24);",
+     "((uint32_t)(sum[4 * p + 2] / n) << 16);"),
+    ("hqs_blue_from_green", "sum[4 * (uint64_t)pix + 2] += (c >> 16) & 255u;",
+     "sum[4 * (uint64_t)pix + 2] += (c >> 8) & 255u;"),
+    ("hqs_red_plus_alpha", "sum[4 * (uint64_t)pix + 0] += c & 255u;",
+     "sum[4 * (uint64_t)pix + 0] += (c & 255u) + (c >> 24);"),
+    ("hqs_window_from_own_depth", "float limit = wmin * 1.01f;", "float limit = w * 1.01f;"),
+    ("hqs_fixed_k3",
+     "        int k = or_select_k(B, v);\n        for (uint32_t j = 0; j < B->count; ++j)\n"
+     "            hqs_point(B, k, B->first + j, w1, w2, w3, color, v, vis, sum);\n    }\n"
+     "    hqs_average(sum, npix, out);\n    free(sum);\n}",
+     "        int k = 3;\n        for (uint32_t j = 0; j < B->count; ++j)\n"
+     "            hqs_point(B, k, B->first + j, w1, w2, w3, color, v, vis, sum);\n    }\n"
+     "    hqs_average(sum, npix, out);\n    free(sum);\n}"),
+    ("hqs_lod_fixed_k3",
+     "        const or_batch* B = &nodes[i];\n        int k = or_select_k(B, v);\n"
+     "        for (uint32_t j = 0; j < B->count; ++j)\n            hqs_point",
+     "        const or_batch* B = &nodes[i];\n        int k = 3;\n"
+     "        for (uint32_t j = 0; j < B->count; ++j)\n            hqs_point"),
+    ("hqs_threaded_drops_partials",
+     "for (uint64_t q = 0; q < 4 * npix; ++q) jobs[0].sum[q] += jobs[t].sum[q];",
+     "for (uint64_t q = 0; q < 4 * npix; ++q) jobs[0].sum[q] += 0;"),
+    ("hqs_dilate_radius",
+     "            int r = 1 + or_ring((float)px + 0.5f, (float)py + 0.5f, width, height);\n"
+     "            uint64_t best = OR_EMPTY, at = 0;",
+     "            int r = or_ring((float)px + 0.5f, (float)py + 0.5f, width, height);\n"
+     "            uint64_t best = OR_EMPTY, at = 0;"),
+    ("hqs_dilate_last_not_closest",
+     "                    if (vis[q] < best) {\n                        best = vis[q];",
+     "                    if (vis[q] != OR_EMPTY) {\n                        best = vis[q];"),
 ]
 
 # the full-size encoding checker, checked by tests/test_oracle_verify.py
@@ -117,6 +147,33 @@ VERIFY_MUTANTS = [
     ("verify_lod_no_split_rule", "                         : (nodes[b].count > max_node_points && !last)) { code = 5; *where = b; }",
      "                         : 0) { code = 5; *where = b; }"),
     ("verify_lod_no_order", "(i > B->first && idx <= prev)", "(0)"),
+    ("verify_no_header",
+     "if (B->first != first || B->count != end - first) { j->code = 1; j->where = b; return NULL; }", ";"),
+    ("verify_no_words",
+     "            if (w[0] != j->w1[i] || w[1] != j->w2[i] || w[2] != j->w3[i]) {\n"
+     "                j->code = 5; j->where = i; return NULL;\n            }", ""),
+    ("verify_no_colour", "            if (col != j->color[i]) { j->code = 6; j->where = i; return NULL; }", ""),
+    ("verify_batch_count",
+     "if (batch_size == 0 || n > 0xFFFFFFFFull || nbatches != or_num_batches(n, batch_size)) return 1;",
+     "if (batch_size == 0 || n > 0xFFFFFFFFull) return 1;"),
+    ("verify_lod_no_words",
+     "if (w[0] != j->w1[i] || w[1] != j->w2[i] || w[2] != j->w3[i]) { j->code = 6; j->where = i; return NULL; }",
+     ";"),
+    ("verify_lod_no_colour",
+     "if ((j->rgba ? j->rgba[idx] : 0u) != j->color[i]) { j->code = 7; j->where = i; return NULL; }", ";"),
+    ("verify_lod_no_root",
+     "if (memcmp(&nodes[0].min[c], &lo[c], 4) != 0 || memcmp(&nodes[0].size[c], &side, 4) != 0) return 1;",
+     ";"),
+    ("verify_lod_no_header",
+     "if (nodes[b].first != total || nodes[b].count == 0) { code = 1; *where = b; break; }", ";"),
+    ("verify_lod_no_level",
+     "if (p >= b || (b > 1 && p < parent[b - 1]) || level[b] != level[p] + 1 || level[b] >= max_levels) {",
+     "if (p >= b || (b > 1 && p < parent[b - 1])) {"),
+    ("verify_lod_no_child_cube",
+     "            if (memcmp(&nodes[b].size[c], &half, 4) != 0) { code = 2; *where = b; }", ""),
+    ("verify_lod_no_octant_order",
+     "if (b > 1 && parent[b - 1] == p && oct[b - 1] >= o) { code = 2; *where = b; }", ";"),
+    ("verify_lod_no_total", "if (!code && total != n) { code = 1; *where = nnodes; }", ";"),
 ]
 
 # Sec. 3.5 level of detail and Sec. 3.7 foveation and dilation, checked by the

@@ -156,3 +156,33 @@ def test_lod_rejects_a_leaf_that_should_have_split(tree):
     assert (t3.nodes["count"][t3.level == 2] > M).any()
     code, b = _lod(xyz, rgba, t3, levels=L)
     assert code == 5 and t3.level[b] == 2 and t3.nodes[b]["count"] > M
+
+
+def test_lod_rejects_header_cube_sibling_order_and_count_mistakes(tree):
+    xyz, rgba, t = tree
+    b = int(np.nonzero(t.level == 2)[0][1])
+    # a node whose points do not start where the previous node's end
+    nd = t.nodes.copy()
+    nd[b]["first"] += 1
+    assert _lod(xyz, rgba, t, nodes=nd) == (1, b)
+    # a child cube that is not half of its parent's on one axis
+    nd = t.nodes.copy()
+    nd[b]["size"][1] = np.nextafter(nd[b]["size"][1], np.float32(np.inf))
+    assert _lod(xyz, rgba, t, nodes=nd) == (2, b)
+    # two leaf siblings exchanged (records and point blocks), so that every
+    # node still holds its own cube's points: only the octant order breaks
+    leaves = set(range(len(t.nodes))) - set(int(p) for p in t.parent[1:])
+    s = next(i for i in range(1, len(t.nodes) - 1)
+             if i in leaves and i + 1 in leaves and t.parent[i] == t.parent[i + 1])
+    fa, ca = int(t.nodes[s]["first"]), int(t.nodes[s]["count"])
+    cb = int(t.nodes[s + 1]["count"])
+    nd = t.nodes.copy()
+    nd[s], nd[s + 1] = t.nodes[s + 1], t.nodes[s]
+    nd[s]["first"], nd[s + 1]["first"] = fa, fa + cb
+    order = np.r_[0:fa, fa + ca:fa + ca + cb, fa:fa + ca, fa + ca + cb:len(t.perm)]
+    sw = {k: getattr(t, k)[order].copy() for k in ("perm", "w1", "w2", "w3", "color")}
+    assert _lod(xyz, rgba, t, nodes=nd, **sw) == (2, s + 1)
+    # the last node dropped: its points are missing from the tree
+    k = len(t.nodes) - 1
+    assert _lod(xyz, rgba, t, nodes=t.nodes[:k].copy(), parent=t.parent[:k].copy(),
+                level=t.level[:k].copy()) == (1, k)
