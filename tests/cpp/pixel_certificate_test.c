@@ -1,7 +1,9 @@
 /* Adversarial check of the raster kernel's certified fast pixel stage.
  *
- * The definition (the oracle's, reading 7 and 15): f = fl(fl(fl(c / w) * 0.5
- * + 0.5) * W) with an IEEE divide, then the floor bits fl_down(f + 2^23).
+ * The definition (the oracle's reading of Listing 1's pixel): f =
+ * fl(fl(fl(c / w) * 0.5 + 0.5) * W) with an IEEE divide, then the floor bits
+ * fl_down(f + 2^23), which fall in [2^23, 2^23 + W) exactly for accepted
+ * points.
  *
  * The kernel's fast stage never divides: r is an approximate reciprocal of w
  * (a hardware estimate), refined by one Newton step r' = fma(r, fma(-w, r, 1),
