@@ -7,15 +7,17 @@
  *
  * The kernel's fast stage never divides: r is an approximate reciprocal of w
  * (a hardware estimate), refined by one Newton step r' = fma(r, fma(-w, r, 1),
- * r); q' = fl(c * r'); with eta = 2^-21 it forms u- = fma(q', 0.5, 0.5 - eta)
+ * r) in the general path and used as it is in the fast path of certified
+ * batches; q' = fl(c * r'); with eta = 2^-21 it forms u- = fma(q', 0.5, 0.5 - eta)
  * and u+ = fma(q', 0.5, 0.5 + eta) and the bracket fl_down(u- * W + 2^23),
  * fl_down(u+ * W + 2^23) (fused, rounded down). When both ends agree and
  * 2^-100 <= w <= 2^100 it takes them as the floor bits; otherwise it falls back
  * to the definition.
  *
- * This program takes r as ANY float within a relative distance 2^-20 of 1/w
- * (far looser than the estimate's documented accuracy), flushed to zero below
- * the smallest normal as the estimate does, and checks on random and on
+ * With the Newton step this program takes r as ANY float within a relative
+ * distance 2^-20 of 1/w (far looser than the estimate's documented accuracy of
+ * 1 ulp); without it, any float up to 2 ulps from 1/w. Either is flushed to
+ * zero below the smallest normal as the estimate does, and it checks on random and on
  * pixel-edge inputs that a certified bracket always gives the same
  * accept/reject decision as the definition, and the same bits when accepted.
  *
@@ -80,12 +82,20 @@ static uint32_t exact_floor_bits(float c, float w, float W) {
     return fbits(s);
 }
 
+/* newton: refine r by one Newton step first (the general path); without it
+ * (the fast path of certified batches) r is used as it is. eta: the margin. */
+static int newton = 1;
+static float eta = 0x1p-21f;
+
 static int fast_floor_bits(float c, float w, float W, float r, uint32_t* out) {
-    const float e = fma_rn(-w, r, 1.0f);
-    const float r2 = fma_rn(r, e, r);
+    float r2 = r;
+    if (newton) {
+        const float e = fma_rn(-w, r, 1.0f);
+        r2 = fma_rn(r, e, r);
+    }
     volatile float q = c * r2;
-    const float ulo = fma_rn(q, 0.5f, 0.5f - 0x1p-21f);
-    const float uhi = fma_rn(q, 0.5f, 0.5f + 0x1p-21f);
+    const float ulo = fma_rn(q, 0.5f, 0.5f - eta);
+    const float uhi = fma_rn(q, 0.5f, 0.5f + eta);
     const uint32_t blo = fbits(fma_rd(ulo, W, 8388608.0f));
     const uint32_t bhi = fbits(fma_rd(uhi, W, 8388608.0f));
     *out = blo;
@@ -124,20 +134,38 @@ static float ftz(float r) { return fabsf(r) < 0x1p-126f ? copysignf(0.0f, r) : r
 
 static void with_reciprocals(float c, float w, float W) {
     const float r0 = 1.0f / w;
-    const double d[] = {0.0, 0x1p-20, -0x1p-20, 0x1p-23, -0x1p-23};
-    for (int i = 0; i < 5; ++i) one(c, w, W, ftz((float)((double)r0 * (1.0 + d[i]))));
-    one(c, w, W, ftz((float)((double)r0 * (1.0 + (2.0 * uniform() - 1.0) * 0x1p-20))));
+    if (newton) {
+        /* any float within a relative 2^-20 of 1/w */
+        const double d[] = {0.0, 0x1p-20, -0x1p-20, 0x1p-23, -0x1p-23};
+        for (int i = 0; i < 5; ++i) one(c, w, W, ftz((float)((double)r0 * (1.0 + d[i]))));
+        one(c, w, W, ftz((float)((double)r0 * (1.0 + (2.0 * uniform() - 1.0) * 0x1p-20))));
+    } else {
+        /* no Newton step: the estimate is specified to 1 ulp; this takes every
+         * float up to 2 ulps from the correctly rounded reciprocal, and random
+         * ones within a relative 2^-23 of it */
+        one(c, w, W, ftz(r0));
+        one(c, w, W, ftz(nextafterf(nextafterf(r0, INFINITY), INFINITY)));
+        one(c, w, W, ftz(nextafterf(nextafterf(r0, 0.0f), 0.0f)));
+        one(c, w, W, ftz((float)((double)r0 * (1.0 + (2.0 * uniform() - 1.0) * 0x1p-23))));
+    }
     one(c, w, W, ftz(nextafterf(r0, INFINITY)));
     one(c, w, W, ftz(nextafterf(r0, 0.0f)));
 }
 
-int main(void) {
+int main(int argc, char** argv) {
     /* the rounding helpers against hand-checked cases */
     if (fma_rd(1.0f, 1.0f, 0x1p-30f) != 1.0f || fma_rd(-1.0f, 1.0f, -0x1p-30f) != -1.0f - 0x1p-23f ||
         fma_rn(1.0f, 1.0f, 0x1p-24f) != 1.0f || fma_rn(1.0f, 1.0f, 0x1p-24f + 0x1p-40f) != 1.0f + 0x1p-23f ||
         fma_rn(1.0f + 0x1p-23f, 1.0f, 0x1p-24f) != 1.0f + 0x1p-22f) {
         printf("FAIL rounding helpers\n");
         return 1;
+    }
+    /* argv[1]: "newton" (default), "plain" (no Newton step), or "plain-narrow"
+     * (no Newton step and a margin of 2^-23, which must fail) */
+    if (argc > 1 && strcmp(argv[1], "plain") == 0) newton = 0;
+    if (argc > 1 && strcmp(argv[1], "plain-narrow") == 0) {
+        newton = 0;
+        eta = 0x1p-23f;
     }
     const float Ws[] = {1.0f, 64.0f, 1000.0f, 1080.0f, 1920.0f, 2016.0f, 2240.0f, 3840.0f, 16384.0f};
     for (int wi = 0; wi < 9; ++wi) {
