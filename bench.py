@@ -185,16 +185,20 @@ def cpu_baseline(args, params, m, sample_points, threads=None):
 
 def serving_bench(args, pcr, ctx, clouds):
     """Poisson stream of view requests over resident clouds, served with
-    multi-view batching and with one view per launch; same requests, same
-    bits. Returns the serving summary."""
+    multi-view batching (views per launch tuned per cloud) and with one view
+    per launch; same requests, same bits. First both at a saturating arrival
+    rate (the capacity), then both at 50 % and 90 % of the one-view-per-launch
+    capacity, where p50/p99 measure service latency rather than queue depth.
+    Returns the serving summary, per cloud and overall."""
     import hashlib
     import pcsynth
     rng = np.random.default_rng(args.seed + 101)
     choices = [(1280, 720), (1920, 1080), (3840, 2160), "stereo"]
-    reqs, t = [], 0.0
+    reqs, gaps = [], []
     for i in range(args.serve_requests):
-        t += rng.exponential(1.0 / args.serve_rate)
-        cloud, params, name = clouds[int(rng.integers(len(clouds)))]
+        gaps.append(rng.exponential(1.0))
+        ci = int(rng.integers(len(clouds)))
+        cloud, params, name = clouds[ci]
         c = choices[int(rng.integers(len(choices)))]
         if c == "stereo":
             W, H = 2016, 2240
@@ -204,9 +208,17 @@ def serving_bench(args, pcr, ctx, clouds):
             W, H = c
             views = [pcr.make_view(pcsynth.random_view(params, i, W, H, seed=args.seed), W, H,
                                    pcr.PC_VIEW_CULL)]
-        reqs.append((t, cloud, views))
+        reqs.append((ci, cloud, views))
+    nviews = sum(len(v) for _, _, v in reqs)
+    views_per_req = nviews / len(reqs)
+    # each cloud tuned on a bundle of its own views: launch shape and views per launch
+    tuned = {}
+    for ci, (cloud, params, name) in enumerate(clouds):
+        sample = [pcr.make_view(pcsynth.random_view(params, 900 + k, 1920, 1080, seed=args.seed),
+                                1920, 1080, pcr.PC_VIEW_CULL) for k in range(8)]
+        tuned[name] = pcr.pc_autotune(ctx.h, cloud, sample)
 
-    def run(vpl):
+    def run(vpl, rate):
         pcr.pc_set_views_per_launch(ctx.h, vpl)
         tickets, results = [], [None] * len(reqs)
         lock = threading.Condition()
@@ -234,7 +246,9 @@ def serving_bench(args, pcr, ctx, clouds):
         th = threading.Thread(target=collect)
         th.start()
         t0 = time.perf_counter()
-        for ta, cloud, views in reqs:
+        ta = 0.0
+        for gap, (_, cloud, views) in zip(gaps, reqs):
+            ta += gap / rate
             d = ta - (time.perf_counter() - t0)
             if d > 0:
                 time.sleep(d)
@@ -256,24 +270,41 @@ def serving_bench(args, pcr, ctx, clouds):
         t_sub = min(r[0] for r in results)
         t_done = max(r[1] for r in results)
         lat = np.array([r[1] - r[0] for r in results])
-        nviews = sum(len(v) for _, _, v in reqs)
-        return {"views_per_s": nviews / ((t_done - t_sub) / 1e3),
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "ok": all(r[3] == pcr.PC_OK for r in results)}, [r[2] for r in results]
+        out = {"offered_req_per_s": rate, "views_per_s": nviews / ((t_done - t_sub) / 1e3),
+               "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "ok": all(r[3] == pcr.PC_OK for r in results), "per_cloud": {}}
+        for ci, (_, _, name) in enumerate(clouds):
+            sel = np.array([r[0] == ci for r in reqs])
+            if sel.any():
+                out["per_cloud"][name] = {"requests": int(sel.sum()),
+                                          "p50_ms": float(np.percentile(lat[sel], 50)),
+                                          "p99_ms": float(np.percentile(lat[sel], 99))}
+        return out, [r[2] for r in results]
 
-    run(32)   # warm-up: streams, pools, graphs
-    batched, hb = run(32)
-    single, hs = run(1)
-    pcr.pc_set_views_per_launch(ctx.h, 32)
-    return {"requests": len(reqs), "views": sum(len(v) for _, _, v in reqs),
-            "offered_rate_req_per_s": args.serve_rate,
+    saturate = args.serve_rate
+    run(0, saturate)   # warm-up: streams, pools, graphs
+    batched, hb = run(0, saturate)       # per-cloud tuned views per launch
+    single, hs = run(1, saturate)
+    capacity_req = single["views_per_s"] / views_per_req
+    loads = {}
+    same = hb == hs
+    for frac in (0.5, 0.9):
+        b, hb2 = run(0, frac * capacity_req)
+        s1, hs2 = run(1, frac * capacity_req)
+        same = same and hb2 == hb and hs2 == hb
+        loads[f"{int(frac * 100)}pct_of_one_view_capacity"] = {"batched": b, "one_view_per_launch": s1}
+    pcr.pc_set_views_per_launch(ctx.h, 0)
+    return {"requests": len(reqs), "views": nviews,
             "clouds": [c[2] for c in clouds],
             "resolutions": "1280x720 / 1920x1080 / 3840x2160 / stereo 2x2016x2240, uniform",
+            "tuned": tuned,
+            "saturating_offered_req_per_s": saturate,
             "views_per_s": batched["views_per_s"], "p50_ms": batched["p50_ms"],
-            "p99_ms": batched["p99_ms"],
+            "p99_ms": batched["p99_ms"], "saturated": batched,
             "one_view_per_launch": single,
             "speedup_vs_one_view_per_launch": batched["views_per_s"] / single["views_per_s"],
-            "identical_bits": hb == hs, "all_ok": batched["ok"] and single["ok"]}
+            "sustainable": loads,
+            "identical_bits": same, "all_ok": batched["ok"] and single["ok"]}
 
 
 def small_configs_bench(args, pcr, torch, ctx):
@@ -393,7 +424,7 @@ def multiview_bench(args, pcr, torch, ctx, cloud, params):
                            1280, 720, pcr.PC_VIEW_CULL) for i in range(16)]
     out["terrain_10m_bundle_16x720p"] = compare(terr, views, 20)
     pcr.pc_release_cloud(ctx.h, terr)
-    pcr.pc_set_views_per_launch(ctx.h, 32)
+    pcr.pc_set_views_per_launch(ctx.h, 0)
     return out
 
 

@@ -208,6 +208,10 @@ pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
                                               down) with alpha 255. Exact up to 16,843,009 points
                                               per pixel; beyond, the resolve raises the device
                                               error flag (PC_EDEVICE) */
+#define PC_VIEW_SIGNED_EMPTY   0x200u      /* pixels no point reached hold 2^63 - 1 instead of
+                                              2^64 - 1, so that a signed 64-bit minimum (MPI or
+                                              torch.distributed MIN on int64) merges shards
+                                              exactly: every point's key is below 2^63 */
 #define PC_VIEW_HQS_PACKED     0x100u      /* the same with one 64-bit atomic add per point into
                                               18-bit sums and a 10-bit count; a pixel that gets
                                               more than 1023 points is summed again by a second
@@ -263,19 +267,53 @@ pc_status pc_render(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t 
  * caller-owned vis and rgba (rgba may be NULL), stream-ordered and
  * asynchronous, with precision threshold precision_px (512 is the default of
  * pc_config). It allocates nothing: its scratch (draw list, counters) is a
- * static device array of about 3 MB that every GPU loading the library holds
+ * static device array of about 4 MB that every GPU loading the library holds
  * until the process exits, so a cloud may have at most
  * 131,072 - n_points / 2^20 - 1 batches; larger ones get PC_EINVAL, as do
- * misaligned or missing buffers; views with high-quality shading get
- * PC_ENOTSUP (their sum buffer would need memory). The first call on a device looks up that
- * array's device address (a runtime call, no allocation); make that first
- * call before any stream capture. All calls share the array and reset its
+ * missing buffers and any buffer (batches included) that is not 16-byte
+ * aligned, all refused on the host before anything is launched; views with
+ * high-quality shading get PC_ENOTSUP (their sum buffer would need memory).
+ * device_error (host memory, two words, may be NULL): the call ends by copying
+ * the kernels' error flag and its value there, stream-ordered; once the stream
+ * has reached that point, a nonzero first word means the image is not valid
+ * (a batch outside the point buffers, batches that overlap so that the draw
+ * list overflows). Pinned memory keeps the copy asynchronous; pageable memory
+ * makes the call wait for the stream and cannot be used during a capture.
+ * The first call on a device looks up that
+ * array's device address (a runtime call, no allocation) and keeps it for the
+ * life of the process; make that first call before any stream capture, and do
+ * not reset the device (cudaDeviceReset) after it. All calls share the array and reset its
  * counters, so calls that overlap on the GPU (different streams, or different
  * host threads without ordering) race and corrupt each other's results. */
 pc_status pc_render_noalloc(const pc_batch* batches, uint64_t nbatches,
                             const uint32_t* w1, const uint32_t* w2, const uint32_t* w3,
                             const uint32_t* color, uint64_t n_points, const pc_view* view,
-                            uint64_t* vis, uint32_t* rgba, float precision_px, void* stream);
+                            uint64_t* vis, uint32_t* rgba, float precision_px,
+                            uint32_t* device_error, void* stream);
+
+/* Render one shard of a frame: as pc_render, but only batches
+ * [first_batch, first_batch + batch_count) of the cloud (Sec. 3.2: batches are
+ * drawn independently). Frames split into disjoint ranges merge exactly by the
+ * element-wise minimum of their visibility buffers (pc_merge_min, or a MIN
+ * reduction across GPUs with PC_VIEW_SIGNED_EMPTY), after which pc_resolve
+ * writes the image; rgba may be NULL here to skip each shard's own resolve.
+ * Plain clouds only (PC_ENOTSUP for LOD clouds and high-quality shading);
+ * PC_EINVAL for an empty range or one outside the cloud. */
+pc_status pc_render_range(pc_ctx* ctx, pc_cloud cloud, uint64_t first_batch,
+                          uint64_t batch_count, const pc_view* views, uint32_t nviews,
+                          const pc_framebuffer* fbs, void* stream);
+
+/* Resolve visibility buffers that were filled earlier (shards merged by
+ * pc_merge_min or by a reduction across GPUs) into their rgba images (required
+ * here), stream-ordered: the colour of each pixel's key, 0 where the pixel holds
+ * the empty key of its view's flags; PC_VIEW_DILATE applies. */
+pc_status pc_resolve(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
+                     const pc_framebuffer* fbs, void* stream);
+
+/* dst[i] = min(dst[i], src[i]) for n visibility keys (device, 16-byte aligned,
+ * unsigned compare), stream-ordered: merges two shards of one frame rendered
+ * with the same empty key. PC_EINVAL for null or misaligned buffers. */
+pc_status pc_merge_min(uint64_t* dst, const uint64_t* src, uint64_t n, void* stream);
 
 /* End-to-end variant: renders into library-owned device framebuffers and
  * copies each view's RGBA image into host_rgba[v] (host, width*height
@@ -316,8 +354,10 @@ typedef struct {
 /* Time candidate raster launch shapes (threads per block, blocks per SM,
  * points per warp grab) on views[0], then candidate views per launch on all
  * nviews views, all on `stream` with library-owned framebuffers, and keep the
- * fastest for later pc_render and serving launches on this context (fields set
- * in pc_config override it). Results are identical for every candidate; only
+ * fastest for later pc_render and serving launches of this cloud (a small
+ * cloud gains from many views per launch, a large one may not): the launch
+ * shape (fields set in pc_config override it) and the views per launch
+ * (unless pc_set_views_per_launch has set one for the context). Results are identical for every candidate; only
  * the time differs. Synchronous. Renders and serving groups that other threads
  * launch on this context meanwhile stay correct but take the candidate being
  * timed, and their time skews the measurement: tune on an idle context. */
@@ -325,8 +365,9 @@ pc_status pc_autotune(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_
                       void* stream, pc_tune_result* out);
 
 /* Set the views rendered by one launch (1..32) for later pc_render calls and
- * serving groups on this context, replacing the autotuner's choice. 1 gives
- * one view per launch. */
+ * serving groups of every cloud on this context, in place of the autotuner's
+ * per-cloud choices; 1 gives one view per launch, 0 goes back to the per-cloud
+ * choices (the configured maximum for clouds never tuned). */
 pc_status pc_set_views_per_launch(pc_ctx* ctx, uint32_t views_per_launch);
 
 /* ---- timing (per-pass CUDA events) --------------------------------------- */
@@ -371,7 +412,9 @@ typedef struct {
 pc_status pc_submit(pc_ctx* ctx, pc_cloud cloud, const pc_view* views, uint32_t nviews,
                     const pc_framebuffer* fbs, pc_ticket* out);
 
-/* Wait up to timeout_ms (0 = just test, < 0 = no limit) for a request.
+/* Wait up to timeout_ms for a request: 0 = just test; values above 60000 wait
+ * 60000 ms, so a call never blocks longer than a minute, even when the
+ * request's stream never finishes; a negative timeout is PC_EINVAL.
  * PC_ETIMEDOUT if it has not finished; on PC_OK *out describes the result. */
 pc_status pc_poll(pc_ctx* ctx, pc_ticket ticket, int32_t timeout_ms, pc_result* out);
 

@@ -32,6 +32,8 @@ PC_VIEW_NO_EARLY_DEPTH = 2
 PC_VIEW_DILATE = 0x40
 PC_VIEW_HQS = 0x80
 PC_VIEW_HQS_PACKED = 0x100
+PC_VIEW_SIGNED_EMPTY = 0x200
+EMPTY_SIGNED = 0x7FFFFFFFFFFFFFFF
 EMPTY = 0xFFFFFFFFFFFFFFFF
 
 
@@ -138,9 +140,13 @@ SIGNATURES = [
     ("pc_lod_encode", _i32, [_vp, _vp, _u64, _P(pc_lod_opts), _u32, _u64, _vp, _vp, _vp,
                              _P(_u64), _vp, _vp, _vp, _vp, _vp]),
     ("pc_render", _i32, [_vp, _u64, _P(pc_view), _u32, _P(pc_framebuffer), _vp]),
+    ("pc_render_range", _i32, [_vp, _u64, _u64, _u64, _P(pc_view), _u32, _P(pc_framebuffer),
+                               _vp]),
+    ("pc_resolve", _i32, [_vp, _u64, _P(pc_view), _u32, _P(pc_framebuffer), _vp]),
+    ("pc_merge_min", _i32, [_vp, _vp, _u64, _vp]),
     ("pc_render_host", _i32, [_vp, _u64, _P(pc_view), _u32, _P(_vp), _vp]),
     ("pc_render_noalloc", _i32, [_vp, _u64, _vp, _vp, _vp, _vp, _u64, _P(pc_view), _vp, _vp,
-                                 ctypes.c_float, _vp]),
+                                 ctypes.c_float, _vp, _vp]),
     ("pc_get_view_stats", _i32, [_vp, _vp, _u32, _P(pc_view_stats)]),
     ("pc_autotune", _i32, [_vp, _u64, _P(pc_view), _u32, _vp, _P(pc_tune_result)]),
     ("pc_set_views_per_launch", _i32, [_vp, _u32]),
@@ -376,6 +382,50 @@ def pc_render(ctx: int, cloud: int, views, fbs, stream: int = 0) -> None:
     _check(ctx, lib().pc_render(ctx, cloud, va, len(views), fa, stream))
 
 
+def pc_render_range(ctx: int, cloud: int, first_batch: int, batch_count: int, views, fbs,
+                    stream: int = 0) -> None:
+    """One shard of a frame: batches [first_batch, first_batch + batch_count).
+    fbs: (vis_ptr, rgba_ptr or None) device pointers per view."""
+    va = _views_arr(views)
+    fa = (pc_framebuffer * len(views))()
+    for i, (vis, rgba) in enumerate(fbs):
+        fa[i] = pc_framebuffer(vis, rgba)
+    _check(ctx, lib().pc_render_range(ctx, cloud, first_batch, batch_count, va, len(views), fa,
+                                      stream))
+
+
+def pc_resolve(ctx: int, cloud: int, views, fbs, stream: int = 0) -> None:
+    """Resolve merged visibility buffers into their images (fbs as for pc_render)."""
+    va = _views_arr(views)
+    fa = (pc_framebuffer * len(views))()
+    for i, (vis, rgba) in enumerate(fbs):
+        fa[i] = pc_framebuffer(vis, rgba)
+    _check(ctx, lib().pc_resolve(ctx, cloud, va, len(views), fa, stream))
+
+
+def pc_merge_min(dst: int, src: int, n: int, stream: int = 0) -> None:
+    """dst[i] = min(dst[i], src[i]) over n keys (device pointers)."""
+    _check(None, lib().pc_merge_min(dst, src, n, stream))
+
+
+def batch_range(n_batches: int, rank: int, world: int):
+    """(first, count): the contiguous batch range of one rank when a frame's
+    batches are split over `world` ranks as evenly as possible (Sec. 3.2:
+    batches are independent, so the shards merge by a minimum of keys)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError(f"rank {rank} outside a world of {world}")
+    first = n_batches * rank // world
+    return first, n_batches * (rank + 1) // world - first
+
+
+def merge_shards(vis, group=None) -> None:
+    """Element-wise minimum of one visibility buffer (int64 torch tensor,
+    rendered with PC_VIEW_SIGNED_EMPTY) over the ranks of a process group, in
+    place: the exchange step of a frame split by batch ranges."""
+    import torch.distributed as dist
+    dist.all_reduce(vis, op=dist.ReduceOp.MIN, group=group)
+
+
 def pc_render_host(ctx: int, cloud: int, views, out_images, stream: int = 0) -> None:
     """out_images: list of writable numpy uint32 arrays (width*height each)."""
     if len(out_images) != len(views):
@@ -431,9 +481,10 @@ def pc_submit(ctx: int, cloud: int, views, fbs=None) -> int:
     return out.value
 
 
-def pc_poll(ctx: int, ticket: int, timeout_ms: int = -1):
+def pc_poll(ctx: int, ticket: int, timeout_ms: int = 10000):
     """Returns (status, result) — status PC_OK or PC_ETIMEDOUT; result holds
-    numpy copies of the images when PC_OK."""
+    numpy copies of the images when PC_OK. timeout_ms: 0..60000 (larger values
+    wait 60 s; negative ones raise)."""
     r = pc_result()
     rc = lib().pc_poll(ctx, ticket, timeout_ms, ctypes.byref(r))
     if rc == PC_ETIMEDOUT:
@@ -510,6 +561,37 @@ class Context:
         pc_render(self.h, cloud, views, [(a.data_ptr(), b.data_ptr()) for a, b in fbs],
                   s.cuda_stream)
         return fbs
+
+    def render_range(self, cloud, first_batch, batch_count, views, fbs=None, stream=None):
+        """One shard (a batch range) of each view into torch framebuffers."""
+        import torch
+        if fbs is None:
+            fbs = self.framebuffers(views)
+        elif not (isinstance(fbs, _Framebuffers) and fbs.fits(views, self.device)):
+            _check_framebuffers(views, fbs, self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        pc_render_range(self.h, cloud, first_batch, batch_count, views,
+                        [(a.data_ptr(), b.data_ptr()) for a, b in fbs], s.cuda_stream)
+        return fbs
+
+    def resolve(self, cloud, views, fbs, stream=None):
+        """The images of visibility buffers filled (and merged) earlier."""
+        import torch
+        if not (isinstance(fbs, _Framebuffers) and fbs.fits(views, self.device)):
+            _check_framebuffers(views, fbs, self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        pc_resolve(self.h, cloud, views, [(a.data_ptr(), b.data_ptr()) for a, b in fbs],
+                   s.cuda_stream)
+        return fbs
+
+    def merge_min(self, dst, src, stream=None):
+        """dst <- min(dst, src) for two int64 visibility tensors of one size."""
+        import torch
+        if dst.numel() != src.numel() or dst.dtype != torch.int64 or src.dtype != torch.int64:
+            raise ValueError("merge_min needs two int64 visibility buffers of one size")
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        pc_merge_min(dst.data_ptr(), src.data_ptr(), dst.numel(), s.cuda_stream)
+        return dst
 
     def stats(self, view=0, stream=None):
         import torch

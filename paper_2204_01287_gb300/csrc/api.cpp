@@ -159,18 +159,20 @@ std::shared_ptr<Cloud> Ctx::find_cloud(pc_cloud h) {
     return it == clouds.end() ? nullptr : it->second;
 }
 
-Tune Ctx::tune_for(uint32_t nviews) const {
+Tune Ctx::tune_for(const Cloud& cl, uint32_t nviews) const {
     std::lock_guard<std::mutex> g(tune_mu);
-    return tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
+    return cl.tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)];
 }
 
-void Ctx::set_tune(uint32_t nviews, const Tune& t) {
+void Ctx::set_tune(Cloud& cl, uint32_t nviews, const Tune& t) {
     std::lock_guard<std::mutex> g(tune_mu);
-    tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)] = t;
+    cl.tune[std::min<uint32_t>(nviews, kMaxViewsPerLaunch)] = t;
 }
 
-RasterShape Ctx::shape_for(uint32_t nviews) {
-    const Tune t = tune_for(nviews);
+// The cloud's tuned launch shape (pc_config fields override it); untuned: 256
+// threads and as many resident blocks as the kernel allows.
+RasterShape Ctx::shape_for(const Cloud& cl, uint32_t nviews) {
+    const Tune t = tune_for(cl, nviews);
     RasterShape r;
     r.threads_per_block = cfg.threads_per_block ? (int)cfg.threads_per_block
                           : t.threads_per_block ? t.threads_per_block : 256;
@@ -186,7 +188,7 @@ RasterShape Ctx::shape_for(uint32_t nviews) {
 // every resident raster warp about four segments. LOD frames draw a small part
 // of their cloud, so they take the smallest size.
 uint32_t Ctx::seg_points_for(uint32_t nviews, const Cloud& cl, const RasterShape& shape) const {
-    const Tune t = tune_for(nviews);
+    const Tune t = tune_for(cl, nviews);
     const uint32_t seg = t.seg_points ? t.seg_points : kSegmentPoints;
     if (cl.is_lod) return kMinSegmentPoints;
     const uint64_t warps = std::max<uint64_t>(1, (uint64_t)shape.blocks * shape.threads_per_block / 32);
@@ -194,17 +196,25 @@ uint32_t Ctx::seg_points_for(uint32_t nviews, const Cloud& cl, const RasterShape
     return (uint32_t)std::max<uint64_t>(kMinSegmentPoints, std::min<uint64_t>(seg, fit));
 }
 
-uint32_t Ctx::views_per_launch() const {
-    const uint32_t t = tuned_views_per_launch.load();
-    uint32_t v = t ? t : cfg.max_views_per_launch;
+// Views per launch for a cloud: pc_set_views_per_launch's value when one is
+// set, else the autotuner's choice for this cloud, else the configured maximum.
+uint32_t Ctx::views_per_launch(const Cloud& cl) const {
+    const uint32_t f = forced_vpl.load(), t = cl.tuned_vpl.load();
+    uint32_t v = f ? f : t ? t : cfg.max_views_per_launch;
     return std::max<uint32_t>(1, std::min<uint32_t>(v, kMaxViewsPerLaunch));
 }
 
 // The kernels of one frame: per launch group, clear / cull / raster / resolve.
 pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nviews,
                             const pc_framebuffer* fbs, cudaStream_t st, Slot* slot,
-                            uint32_t maxv, bool timing) {
-    const CloudView cv = cl.view();
+                            uint32_t maxv, bool timing, const FrameOpts& fo) {
+    CloudView cv = cl.view();
+    if (fo.first || fo.count < cl.n_batches) {
+        // a shard: the kernels see only the batches of the range (their point
+        // indices stay those of the whole cloud)
+        cv.batches += fo.first;
+        cv.n_batches = (uint32_t)std::min<uint64_t>(fo.count, cl.n_batches - fo.first);
+    }
     for (uint32_t base = 0; base < nviews; base += maxv) {
         uint64_t accum_off = 0;
         bool shade = false;
@@ -212,7 +222,7 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
         std::memset(&vt, 0, sizeof vt);
         vt.n = std::min(maxv, nviews - base);
         vt.threshold_px = cfg.precision_px;
-        const RasterShape shape = shape_for(vt.n);
+        const RasterShape shape = shape_for(cl, vt.n);
         vt.seg_points = seg_points_for(vt.n, cl, shape);
         for (uint32_t j = 0; j < vt.n; ++j) {
             const pc_view& pv = views[base + j];
@@ -244,7 +254,16 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
             for (auto& ev : fe->ev) cudaEventCreate(&ev);
             cudaEventRecord(fe->ev[0], st);
         }
-        cudaError_t e = launch_clear(vt, base, slot->scratch, st);
+        cudaError_t e = cudaSuccess;
+        if (fo.resolve_only) {
+            if (fe) for (int i = 1; i < 5; ++i) cudaEventRecord(fe->ev[i], st);
+            e = launch_resolve(cv, vt, slot->scratch, st);
+            if (e != cudaSuccess) return cuda_fail(e, "resolve launch");
+            if (fe) cudaEventRecord(fe->ev[5], st);
+            launches += 1;
+            continue;
+        }
+        e = launch_clear(vt, base, slot->scratch, st);
         if (e != cudaSuccess) return cuda_fail(e, "clear launch");
         if (fe) cudaEventRecord(fe->ev[1], st);
         if (cl.is_lod) {
@@ -279,10 +298,29 @@ pc_status Ctx::launch_frame(const Cloud& cl, const pc_view* views, uint32_t nvie
 // a CUDA graph that is updated in place and replayed; a frame with the same
 // launch layout reuses the instantiated graph.
 pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
-                      const pc_framebuffer* fbs, cudaStream_t st, Slot* slot) {
+                      const pc_framebuffer* fbs, cudaStream_t st, Slot* slot,
+                      const FrameOpts& fo) {
     if (!views || !fbs || nviews == 0 || nviews > kMaxViewsPerRender) {
         fail_msg("pc_render: need 1..%u views and framebuffers", kMaxViewsPerRender);
         return PC_EINVAL;
+    }
+    const bool shard = fo.first != 0 || fo.count < cl.n_batches || fo.resolve_only;
+    if (shard) {
+        if (fo.first > cl.n_batches || (fo.count != ~0ull && fo.first + fo.count > cl.n_batches)) {
+            fail_msg("batch range %llu + %llu outside the cloud's %llu batches",
+                     (unsigned long long)fo.first, (unsigned long long)fo.count,
+                     (unsigned long long)cl.n_batches);
+            return PC_EINVAL;
+        }
+        if (cl.is_lod) {
+            fail_msg("batch ranges and separate resolves need a plain cloud (not LOD)");
+            return PC_ENOTSUP;
+        }
+        for (uint32_t v = 0; v < nviews; ++v)
+            if (hqs_mode(views[v].flags)) {
+                fail_msg("view %u: high-quality shading needs the whole frame in one call", v);
+                return PC_ENOTSUP;
+            }
     }
     for (uint32_t v = 0; v < nviews; ++v) {
         const pc_view& pv = views[v];
@@ -297,7 +335,7 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
     }
     if (!slot) slot = slot_for(st);
     std::lock_guard<std::mutex> sg(slot->mu);
-    const uint32_t maxv = views_per_launch();   // one value for the whole call
+    const uint32_t maxv = views_per_launch(cl);   // one value for the whole call
     pc_status rc = ensure_capacity(*slot, cl.n_entries, cl.is_lod ? cl.n_batches : 0);
     if (rc == PC_OK) rc = ensure_hqs(*slot, views, nviews, maxv);
     if (rc != PC_OK) return rc;
@@ -310,7 +348,7 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     }
-    rc = launch_frame(cl, views, nviews, fbs, st, slot, maxv, timing);
+    rc = launch_frame(cl, views, nviews, fbs, st, slot, maxv, timing, fo);
     if (graph) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(st, &g);
@@ -322,7 +360,7 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
         uint64_t shaded = 0;   // the views with a colour pass change the launch layout
         for (uint32_t v = 0; v < nviews; ++v) shaded |= (uint64_t)(hqs_mode(views[v].flags) != 0);
         const uint64_t key = ((uint64_t)nviews << 8) | maxv | ((uint64_t)cl.is_lod << 40) |
-                             (shaded << 41);
+                             (shaded << 41) | ((uint64_t)fo.resolve_only << 42);
         cudaGraphExec_t& exec = slot->graphs[key];
         if (exec) {
             cudaGraphExecUpdateResultInfo info;
@@ -342,8 +380,10 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     }
     if (rc != PC_OK) return rc;
-    slot->last_nviews = nviews;
-    slot->last_total_batches = cl.n_batches;
+    if (!fo.resolve_only) {
+        slot->last_nviews = nviews;
+        slot->last_total_batches = std::min<uint64_t>(fo.count, cl.n_batches - fo.first);
+    }
     return PC_OK;
 }
 
@@ -635,6 +675,58 @@ pc_status pc_render(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nv
     }
     cudaSetDevice(ctx->device);
     return ctx->render(*cl, views, nviews, fbs, (cudaStream_t)stream, nullptr);
+}
+
+pc_status pc_render_range(pc_ctx* h, pc_cloud cloud, uint64_t first_batch, uint64_t batch_count,
+                          const pc_view* views, uint32_t nviews, const pc_framebuffer* fbs,
+                          void* stream) {
+    if (!h) return PC_EINVAL;
+    Ctx* ctx = reinterpret_cast<Ctx*>(h);
+    auto cl = ctx->find_cloud(cloud);
+    if (!cl) {
+        ctx->fail_msg("pc_render_range: unknown cloud %llu", (unsigned long long)cloud);
+        return PC_ENOTFOUND;
+    }
+    if (batch_count == 0 || first_batch + batch_count > cl->n_batches ||
+        first_batch + batch_count < first_batch) {
+        ctx->fail_msg("pc_render_range: batches %llu + %llu outside 0..%llu",
+                      (unsigned long long)first_batch, (unsigned long long)batch_count,
+                      (unsigned long long)cl->n_batches);
+        return PC_EINVAL;
+    }
+    cudaSetDevice(ctx->device);
+    FrameOpts fo;
+    fo.first = first_batch;
+    fo.count = batch_count;
+    return ctx->render(*cl, views, nviews, fbs, (cudaStream_t)stream, nullptr, fo);
+}
+
+pc_status pc_resolve(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nviews,
+                     const pc_framebuffer* fbs, void* stream) {
+    if (!h) return PC_EINVAL;
+    Ctx* ctx = reinterpret_cast<Ctx*>(h);
+    auto cl = ctx->find_cloud(cloud);
+    if (!cl) {
+        ctx->fail_msg("pc_resolve: unknown cloud %llu", (unsigned long long)cloud);
+        return PC_ENOTFOUND;
+    }
+    if (fbs)
+        for (uint32_t v = 0; v < nviews && views; ++v)
+            if (!fbs[v].rgba) {
+                ctx->fail_msg("pc_resolve: view %u has no rgba buffer", v);
+                return PC_EINVAL;
+            }
+    cudaSetDevice(ctx->device);
+    FrameOpts fo;
+    fo.resolve_only = true;
+    return ctx->render(*cl, views, nviews, fbs, (cudaStream_t)stream, nullptr, fo);
+}
+
+pc_status pc_merge_min(uint64_t* dst, const uint64_t* src, uint64_t n, void* stream) {
+    if (n == 0) return PC_OK;
+    if (!dst || !src || ((uintptr_t)dst & 15) || ((uintptr_t)src & 15)) return PC_EINVAL;
+    return launch_merge_min(dst, src, n, (cudaStream_t)stream) == cudaSuccess ? PC_OK
+                                                                               : PC_ECUDA;
 }
 
 pc_status pc_render_host(pc_ctx* h, pc_cloud cloud, const pc_view* views, uint32_t nviews,

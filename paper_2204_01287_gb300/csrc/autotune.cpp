@@ -1,7 +1,9 @@
-// autotune.cpp — pc_autotune: picks the raster launch shape (threads per block,
-// resident blocks per SM, points per warp grab) and the views per multi-view
-// launch by timing candidates with CUDA events on the caller's stream. Every
-// candidate renders the same bits; only the time differs.
+// autotune.cpp — pc_autotune: picks, for one cloud, the raster launch shape
+// (threads per block, resident blocks per SM, points per warp grab) and the
+// views per multi-view launch by timing candidates with CUDA events on the
+// caller's stream. Every candidate renders the same bits; only the time
+// differs. The choices are kept with the cloud: a 10M-point cloud and a
+// 2B-point cloud on one context want different shapes and views per launch.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -81,16 +83,19 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
     }
     const bool timing = ctx.timing_on;
     ctx.timing_on = false;
-    const uint32_t saved_vpl = ctx.tuned_views_per_launch.load();
+    // candidates run with the context's override cleared and this cloud's
+    // views per launch set; both are restored or replaced at the end
+    const uint32_t saved_forced = ctx.forced_vpl.exchange(0);
+    const uint32_t saved_vpl = cl->tuned_vpl.load();
     std::memset(out, 0, sizeof *out);
 
     // 1. single-view launch shape on views[0]
-    const Tune saved = ctx.tune_for(1);
+    const Tune saved = ctx.tune_for(*cl, 1);
     Tune best = saved;
     double best_ms = 1e30;
     uint32_t cand = 0;
     pc_status rc = PC_OK;
-    ctx.tuned_views_per_launch = 1;
+    cl->tuned_vpl = 1;
     for (int tpb : {128, 256}) {
         const int occ = raster_occupancy(tpb, false);
         for (int bps = std::max(1, occ / 2); bps <= occ && rc == PC_OK; ++bps) {
@@ -99,7 +104,7 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
                 t.threads_per_block = tpb;
                 t.blocks_per_sm = bps;
                 t.seg_points = seg;
-                ctx.set_tune(1, t);
+                ctx.set_tune(*cl, 1, t);
                 double ms = 0;
                 rc = time_render(ctx, *cl, views, 1, fbs.data(), st, slot, 3, ms);
                 if (rc != PC_OK) break;
@@ -117,7 +122,7 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
         for (uint32_t v = 1; v <= kMaxViewsPerLaunch; ++v) {
             Tune t = best;
             if (v > 1) t.blocks_per_sm = 0;   // multi-view kernel: its own occupancy
-            ctx.set_tune(v, t);
+            ctx.set_tune(*cl, v, t);
         }
         out->threads_per_block = (uint32_t)best.threads_per_block;
         out->blocks_per_sm = (uint32_t)best.blocks_per_sm;
@@ -129,7 +134,7 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
     // 2. views per launch over all views
     if (rc == PC_OK && nviews > 1) {
         double single_ms = 0;
-        ctx.tuned_views_per_launch = 1;
+        cl->tuned_vpl = 1;
         rc = time_render(ctx, *cl, views, nviews, fbs.data(), st, slot, 3, single_ms);
         ++cand;
         out->ms_per_view_single = single_ms / nviews;
@@ -137,7 +142,7 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
         uint32_t best_vpl = 1;
         for (uint32_t vpl : {2u, 4u, 8u, 16u, 32u}) {
             if (rc != PC_OK || vpl > std::min<uint32_t>(nviews, ctx.cfg.max_views_per_launch)) break;
-            ctx.tuned_views_per_launch = vpl;
+            cl->tuned_vpl = vpl;
             double ms = 0;
             rc = time_render(ctx, *cl, views, nviews, fbs.data(), st, slot, 3, ms);
             ++cand;
@@ -147,25 +152,26 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
             }
         }
         if (rc == PC_OK) {
-            ctx.tuned_views_per_launch = best_vpl;
+            cl->tuned_vpl = best_vpl;
             out->views_per_launch = best_vpl;
             out->ms_per_view = best_view;
         }
     } else {
-        ctx.tuned_views_per_launch = saved_vpl;
+        cl->tuned_vpl = saved_vpl;
     }
     if (rc != PC_OK) {   // keep the previous choices that were not replaced
-        ctx.tuned_views_per_launch = saved_vpl;
-        if (!shape_chosen) ctx.set_tune(1, saved);
+        cl->tuned_vpl = saved_vpl;
+        if (!shape_chosen) ctx.set_tune(*cl, 1, saved);
     }
+    ctx.forced_vpl = saved_forced;
     out->candidates = cand;
     ctx.timing_on = timing;
     return rc != PC_OK ? rc : ctx.check_device_error(*slot);
 }
 
 extern "C" pc_status pc_set_views_per_launch(pc_ctx* h, uint32_t views_per_launch) {
-    if (!h || views_per_launch == 0 || views_per_launch > kMaxViewsPerLaunch) return PC_EINVAL;
+    if (!h || views_per_launch > kMaxViewsPerLaunch) return PC_EINVAL;
     Ctx& ctx = *reinterpret_cast<Ctx*>(h);
-    ctx.tuned_views_per_launch = views_per_launch;
+    ctx.forced_vpl = views_per_launch;
     return PC_OK;
 }

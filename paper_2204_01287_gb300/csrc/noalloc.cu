@@ -6,6 +6,7 @@
 // from per-stream buffers that the library allocates; this entry point takes
 // it from a file-scope __device__ array instead, so that callers which may not
 // allocate device memory can still render.
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -14,19 +15,36 @@
 namespace pcr {
 namespace {
 
-// Draw-list entries the static scratch holds. Segments are up to 2^20 points,
-// so a cloud needs at most nbatches + n_points / 2^20 + 1 entries.
+// Draw-list entries the static scratch holds. A cloud cut into segments of s
+// points needs at most nbatches + n_points / s + 1 entries; s is the smallest
+// multiple of 128 from kSegmentPoints up that fits, and at most 2^20.
 constexpr uint32_t kNoAllocEntries = 1u << 17;
-constexpr uint32_t kNoAllocSegment = 1u << 20;
+constexpr uint32_t kNoAllocMaxSegment = 1u << 20;
 
 struct NoAllocLayout {
     DrawEntry entries[kNoAllocEntries];
     uint32_t counters[C_COUNT];
     unsigned long long stats[S_COUNT];
 };
+// counters and stats are cleared by one memset, so stats must follow counters
+// with no gap
+static_assert(offsetof(NoAllocLayout, stats) ==
+                  offsetof(NoAllocLayout, counters) + sizeof(uint32_t) * C_COUNT,
+              "stats directly follows counters");
 
-// About 3 MB per device, held by every GPU that loads the library until exit.
+// About 4 MB per device, held by every GPU that loads the library until exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocLayout)];
+
+// Points per draw-list segment for a cloud, or 0 when no segment size up to
+// 2^20 fits the static draw list.
+uint32_t noalloc_segment(uint64_t nbatches, uint64_t n_points) {
+    if (nbatches + 1 >= kNoAllocEntries) return 0;
+    const uint64_t room = kNoAllocEntries - nbatches - 1;   // entries left for splits
+    uint64_t seg = (n_points + room - 1) / room;             // n_points / seg <= room
+    seg = (seg + 127) & ~127ull;
+    if (seg < kSegmentPoints) seg = kSegmentPoints;
+    return seg <= kNoAllocMaxSegment ? (uint32_t)seg : 0u;
+}
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -57,16 +75,17 @@ extern "C" pc_status pc_render_noalloc(const pc_batch* batches, uint64_t nbatche
                                        const uint32_t* w3, const uint32_t* color,
                                        uint64_t n_points, const pc_view* view,
                                        uint64_t* vis, uint32_t* rgba, float precision_px,
-                                       void* stream) {
+                                       uint32_t* device_error, void* stream) {
     if (!view || !vis || (nbatches && !batches)) return PC_EINVAL;
     if (n_points && (!w1 || !w2 || !w3 || !color)) return PC_EINVAL;
     if (n_points >= 0xFFFFFFFFull || !(precision_px > 0.0f)) return PC_EINVAL;
-    if (nbatches + n_points / kNoAllocSegment + 1 > kNoAllocEntries) return PC_EINVAL;
+    const uint32_t seg = noalloc_segment(nbatches, n_points);
+    if (seg == 0) return PC_EINVAL;
     if (view->width == 0 || view->height == 0 || view->width > kMaxDim || view->height > kMaxDim)
         return PC_EINVAL;
     if (hqs_mode(view->flags)) return PC_ENOTSUP;   // the sum buffer would need memory
     const uintptr_t align = (uintptr_t)vis | (uintptr_t)rgba | (uintptr_t)w1 | (uintptr_t)w2 |
-                            (uintptr_t)w3;
+                            (uintptr_t)w3 | (uintptr_t)color | (uintptr_t)batches;
     if (align & 15) return PC_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PC_ECUDA;
@@ -101,7 +120,7 @@ extern "C" pc_status pc_render_noalloc(const pc_batch* batches, uint64_t nbatche
     std::memset(&vt, 0, sizeof vt);
     vt.n = 1;
     vt.threshold_px = precision_px;
-    vt.seg_points = kNoAllocSegment;
+    vt.seg_points = seg;
     std::memcpy(vt.v[0].m, view->view_proj, sizeof vt.v[0].m);
     vt.v[0].width = view->width;
     vt.v[0].height = view->height;
@@ -118,5 +137,10 @@ extern "C" pc_status pc_render_noalloc(const pc_batch* batches, uint64_t nbatche
     if (nbatches && launch_cull(c, vt, 0, s, st) != cudaSuccess) return PC_ECUDA;
     if (nbatches && launch_raster(c, vt, 0, s, shape, st) != cudaSuccess) return PC_ECUDA;
     if (launch_resolve(c, vt, s, st) != cudaSuccess) return PC_ECUDA;
+    // the device error flag and its value, for the caller to read once the
+    // stream has reached this point (a copy into caller memory, no allocation)
+    if (device_error && cudaMemcpyAsync(device_error, L->counters + C_ERROR, 2 * sizeof(uint32_t),
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return PC_ECUDA;
     return PC_OK;
 }

@@ -17,6 +17,13 @@
 
 namespace pcr {
 
+// Launch parameters pc_autotune chose for a cloud, by views per launch.
+struct Tune {
+    int threads_per_block = 0;
+    int blocks_per_sm = 0;
+    uint32_t seg_points = 0;
+};
+
 // A resident cloud: device buffers owned by the library.
 struct Cloud {
     pc_batch* batches = nullptr;
@@ -32,6 +39,9 @@ struct Cloud {
     uint64_t device_bytes = 0;
     uint32_t is_lod = 0;
     uint32_t lod_levels = 0;
+    std::atomic<uint32_t> tuned_vpl{0};   // views per launch pc_autotune chose for this
+                                          // cloud (0: none yet)
+    Tune tune[kMaxViewsPerLaunch + 1];    // its launch shapes (Ctx::tune_mu guards them)
     void free_device();
     CloudView view() const;
     // Device memory goes with the last holder (a queued serving request may
@@ -57,15 +67,17 @@ struct Slot {
     ~Slot();
 };
 
-// Launch parameters chosen by pc_autotune, by views per launch.
-struct Tune {
-    int threads_per_block = 0;
-    int blocks_per_sm = 0;
-    uint32_t seg_points = 0;
-};
-
 struct FrameEvents {
     cudaEvent_t ev[6];   // start, after clear, cull, raster, shade (colour pass), resolve
+};
+
+// What one render call draws: batches [first, first + count) of the cloud (a
+// shard, Sec. 3.2's batches being independent), or, with resolve_only, only
+// the resolve of visibility buffers that earlier calls filled.
+struct FrameOpts {
+    uint64_t first = 0;
+    uint64_t count = ~0ull;
+    bool resolve_only = false;
 };
 
 struct ServeState;   // serve.cpp
@@ -85,10 +97,9 @@ struct Ctx {
     std::deque<FrameEvents> frame_events;
     std::atomic<uint64_t> launches{0};
     std::atomic<uint64_t> raster_launches{0};
-    mutable std::mutex tune_mu;             // guards tune[]: pc_autotune writes it while
-                                            // serving threads may be launching
-    Tune tune[kMaxViewsPerLaunch + 1];      // autotuner results by views per launch
-    std::atomic<uint32_t> tuned_views_per_launch{0};   // 0: cfg.max_views_per_launch
+    mutable std::mutex tune_mu;             // guards the clouds' tune[]: pc_autotune
+                                            // writes it while serving threads launch
+    std::atomic<uint32_t> forced_vpl{0};   // pc_set_views_per_launch (0: per cloud)
     std::atomic<ServeState*> serve{nullptr};   // set once, by the first pc_submit
 
     void fail_msg(const char* fmt, ...);
@@ -98,16 +109,17 @@ struct Ctx {
     std::shared_ptr<Cloud> find_cloud(pc_cloud h);
     pc_status ensure_capacity(Slot& s, uint64_t entries, uint64_t nodes);
     pc_status ensure_hqs(Slot& s, const pc_view* views, uint32_t nviews, uint32_t maxv);
-    RasterShape shape_for(uint32_t nviews);
+    RasterShape shape_for(const Cloud& cl, uint32_t nviews);
     uint32_t seg_points_for(uint32_t nviews, const Cloud& cl, const RasterShape& shape) const;
-    uint32_t views_per_launch() const;
-    Tune tune_for(uint32_t nviews) const;
-    void set_tune(uint32_t nviews, const Tune& t);
+    uint32_t views_per_launch(const Cloud& cl) const;
+    Tune tune_for(const Cloud& cl, uint32_t nviews) const;
+    void set_tune(Cloud& cl, uint32_t nviews, const Tune& t);
     pc_status launch_frame(const Cloud& cl, const pc_view* views, uint32_t nviews,
                            const pc_framebuffer* fbs, cudaStream_t st, Slot* slot, uint32_t maxv,
-                           bool timing);
+                           bool timing, const FrameOpts& fo);
     pc_status render(const Cloud& cl, const pc_view* views, uint32_t nviews,
-                     const pc_framebuffer* fbs, cudaStream_t st, Slot* slot);
+                     const pc_framebuffer* fbs, cudaStream_t st, Slot* slot,
+                     const FrameOpts& fo = FrameOpts());
     pc_status check_device_error(Slot& s);
     pc_cloud register_cloud(const std::shared_ptr<Cloud>& cl);
 };

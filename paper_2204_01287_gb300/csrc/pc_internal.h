@@ -47,6 +47,7 @@ enum : uint32_t {
     E_BATCH_RANGE = 2,     // batch outside the point buffers
     E_INDEX_RANGE = 3,     // visibility key with an index outside the cloud
     E_HQS_OVERFLOW = 4,    // a pixel's colour sums exceeded their field width
+    E_PIXEL_RANGE = 5,     // a certified batch produced a pixel outside its view
 };
 
 // One view as the kernels see it (passed by value in a ViewTable).
@@ -126,7 +127,12 @@ struct DrawEntry {
     uint32_t batch;
     uint32_t seg_first;   // first point of the segment, relative to the batch
     uint32_t seg_count;
+    uint32_t fast_mask;   // bit v: the batch is certified for view v's fast path
+                          // (every point in front of the eye, inside the viewport,
+                          // and decodable with one fused multiply-add per axis)
+    uint32_t pad;
 };
+static_assert(sizeof(DrawEntry) == 32, "draw-list entries are 32 bytes");
 
 // Per-stream scratch memory (device).
 struct Scratch {
@@ -160,6 +166,15 @@ cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_
                          RasterShape shape, cudaStream_t st, int* launched);
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s,
                            cudaStream_t st);
+// dst[i] = min(dst[i], src[i]) over n keys (both 16-byte aligned).
+cudaError_t launch_merge_min(uint64_t* dst, const uint64_t* src, uint64_t n, cudaStream_t st);
+
+// The key of a pixel no point reached: all ones, or, for views with
+// PC_VIEW_SIGNED_EMPTY, the largest signed 64-bit value. Every point's key is
+// below 2^63 (w is a positive finite binary32), so either sorts last.
+PCR_HD inline unsigned long long empty_key(uint32_t flags) {
+    return (flags & PC_VIEW_SIGNED_EMPTY) ? 0x7FFFFFFFFFFFFFFFull : ~0ull;
+}
 // Blocks per SM the raster kernel can keep resident at a block size.
 int raster_occupancy(int threads_per_block, bool multiview);
 

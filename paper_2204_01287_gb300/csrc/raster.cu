@@ -54,11 +54,12 @@ __global__ void k_clear(ViewTable vt, uint32_t view_base, Scratch s) {
     // 16-byte stores; vis is 16-byte aligned (checked on the host)
     ulonglong2* p2 = reinterpret_cast<ulonglong2*>(vp.vis);
     const uint64_t n2 = npix / 2;
-    const ulonglong2 ones = make_ulonglong2(~0ull, ~0ull);
+    const unsigned long long empty = empty_key(vp.flags);
+    const ulonglong2 ones = make_ulonglong2(empty, empty);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
          i += (uint64_t)gridDim.x * blockDim.x)
         p2[i] = ones;
-    if ((npix & 1) && blockIdx.x == 0 && threadIdx.x == 0) vp.vis[npix - 1] = ~0ull;
+    if ((npix & 1) && blockIdx.x == 0 && threadIdx.x == 0) vp.vis[npix - 1] = empty;
     if (vp.accum) {
         // high-quality shading sums <- 0; each view's region is a whole number
         // of 16-byte words
@@ -285,6 +286,53 @@ __device__ __forceinline__ bool cull_batch(const pc_batch& b, const ViewParams& 
     return r < 0 ? cull_batch_exact(b, v) : r == 1;
 }
 
+// Certificate of the raster kernel's fast path for one batch and view. True
+// only if, for every point the batch can decode to (all lie in
+// [min, fl(min + size)]), (1) the binary32 clip w lies in [2^-99, 2^99], so the
+// point is in front of the eye and the reciprocal estimate stays normal,
+// (2) c / w lies in [-1, 1 - 2^-20] on both axes, so the definition's floor
+// pixel is inside the view, and (3) every size is at most 2^100, so that the
+// decode constants 2^23 cell and 2^13 cell are exact. False is always safe: the
+// batch then takes the general path with per-point tests.
+//
+// Bounds in binary32: each row's exact range over the box, widened by 32u times
+// the magnitude of its terms (u = 2^-24). That covers the point's own rounding
+// (at most 6u of the magnitude, as for culling) plus the rounding of these
+// bounds (about 6u more), and 2^-120 covers underflow. The quotient bounds take
+// the interval endpoints (w > 0) and must clear the limits by 2^-12, far more
+// than the binary32 rounding of the bound itself.
+__device__ bool batch_fast(const pc_batch& b, const ViewParams& v) {
+    if (v.flags & PC_VIEW_NO_EARLY_DEPTH) return false;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!(b.size[a] <= 0x1.0p100f)) return false;   // also NaN and infinities
+        lo[a] = b.min[a];
+        hi[a] = __fadd_rn(b.min[a], b.size[a]);
+    }
+    const float* m = v.m;
+    const float X[4] = {m[0], m[4], m[8], m[12]};
+    const float Y[4] = {m[1], m[5], m[9], m[13]};
+    const float Wr[4] = {m[3], m[7], m[11], m[15]};
+    const float g = 32.0f * 0x1.0p-24f, tiny = 0x1.0p-120f;
+    const float mw = __fadd_rn(__fmul_rn(g, row_mag32(Wr, lo, hi)), tiny);
+    const float wl = __fsub_rn(row_min32(Wr, lo, hi), mw);
+    const float wh = __fadd_rn(row_max32(Wr, lo, hi), mw);
+    if (!(wl >= 0x1.0p-99f) || !(wh <= 0x1.0p99f)) return false;
+    const float lim_lo = -1.0f + 0x1.0p-12f, lim_hi = 1.0f - 0x1.0p-12f;
+    const float* rows[2] = {X, Y};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float mr = __fadd_rn(__fmul_rn(g, row_mag32(rows[r], lo, hi)), tiny);
+        const float cl = __fsub_rn(row_min32(rows[r], lo, hi), mr);
+        const float ch = __fadd_rn(row_max32(rows[r], lo, hi), mr);
+        const float qmin = cl >= 0.0f ? __fdiv_rn(cl, wh) : __fdiv_rn(cl, wl);
+        const float qmax = ch >= 0.0f ? __fdiv_rn(ch, wl) : __fdiv_rn(ch, wh);
+        if (!(qmin >= lim_lo) || !(qmax <= lim_hi)) return false;
+    }
+    return true;
+}
+
 constexpr int kCullThreads = 128;
 
 // Sum of a 64-bit value over the 32 lanes of a warp (butterfly on 32-bit
@@ -342,7 +390,7 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
     __syncthreads();
 
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t mask = 0, nseg = 0, count = 0;
+    uint32_t mask = 0, fmask = 0, nseg = 0, count = 0;
     uint64_t kcodes = 0;
     if (b < c.n_batches) {
         const pc_batch bt = c.batches[b];
@@ -374,6 +422,7 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
             const int k = select_k(bt, vp, vt.threshold_px);
             mask |= 1u << v;
             kcodes |= (uint64_t)k << (2 * v);
+            if (k <= 2 && batch_fast(bt, vp)) fmask |= 1u << v;
         }
         if (mask) nseg = (count + vt.seg_points - 1) / vt.seg_points;
     }
@@ -424,6 +473,8 @@ __global__ void __launch_bounds__(kCullThreads) k_cull(CloudView c, ViewTable vt
         DrawEntry e;
         e.kcodes = kcodes;
         e.view_mask = mask;
+        e.fast_mask = fmask;
+        e.pad = 0;
         e.batch = b;
         e.seg_first = g * vt.seg_points;
         e.seg_count = min(vt.seg_points, count - g * vt.seg_points);
@@ -801,6 +852,226 @@ __device__ __forceinline__ uint32_t segment(const CloudView& c, const ViewConst&
     return n_atom;
 }
 
+// ---- k_raster fast path: batches certified by batch_fast ----------------------
+//
+// For a certified batch every point is in front of the eye with w in
+// [2^-99, 2^99] and its floor pixel lies inside the view, so the per-point
+// tests of the general path (w > 0, reciprocal range, pixel range) are known to
+// pass and are left out. The arithmetic is the definition's, in its order:
+//  - decode: fl(X * cell) as one fused multiply-add fma(F, cell, -2^23 cell) on
+//    the binary32 number F = 2^23 + X, whose exact value F cell - 2^23 cell is
+//    X cell (X < 2^23 at k <= 2; the constants are exact since the certificate
+//    bounds the sizes). At k = 1 the y field is read in place: the bits
+//    (w & 0xFFC00) | bits(2^13) are the number 2^13 + Y, with constant
+//    -2^13 cell.
+//  - clip rows: each product as fma(m, x, +0), which differs from fl(m x) only
+//    in the sign of a zero product. A zero's sign cannot change a nonzero sum,
+//    and a zero sum gives the same pixel (c / w = +-0) or no point (w = +-0 is
+//    not > 0), so the pixel and the key are those of the definition. Products
+//    formed this way can feed packed adds: ptxas does not fold an fma into the
+//    add that follows it.
+//  - pixel: the certified bracket of pixel_bits_fast without the Newton step.
+//    rcp.approx is specified to 1 ulp, so q' = fl(c r) is within 3u |q| of c/w
+//    (u = 2^-24) and within 4u |q| of the IEEE quotient; the bracket needs a
+//    margin of about 5u for |q| <= 1.01 and has 2^-21 = 8u. When the two ends
+//    disagree, the point takes the IEEE-divide path.
+
+// Per-view constants of the fast path, as packed pairs of the x and y rows.
+struct FastView {
+    f2_t m01, m45, m89, m1213;   // (m0, m1), (m4, m5), (m8, m9), (m12, m13)
+    f2_t m37;                    // the w row's first two coefficients (m3, m7)
+    float m11, m15;
+    f2_t wh;                     // (W, H)
+    uint32_t width;
+    uint32_t npix;               // width * height
+    unsigned long long* vis;
+};
+
+__device__ __forceinline__ f2_t f2_at(const float* p) {
+    return *reinterpret_cast<const f2_t*>(p);   // two adjacent floats, 8-byte aligned
+}
+
+__device__ __forceinline__ FastView make_fast_view(const ViewParams& v) {
+    FastView f;
+    f.m01 = f2_at(v.m + 0);
+    f.m45 = f2_at(v.m + 4);
+    f.m89 = f2_at(v.m + 8);
+    f.m1213 = f2_at(v.m + 12);
+    f.m37 = f2_pack(v.m[3], v.m[7]);
+    f.m11 = v.m[11];
+    f.m15 = v.m[15];
+    f.wh = f2_pack((float)v.width, (float)v.height);
+    f.width = v.width;
+    f.npix = v.width * v.height;
+    f.vis = reinterpret_cast<unsigned long long*>(v.vis);
+    return f;
+}
+
+// Per-batch decode constants of the fast path at precision K: x and y as a
+// packed pair, z alone; x = min + fma(F, cell, nb).
+struct FastDec {
+    f2_t mn, cell, nb;
+    float mnz, cellz, nbz;
+};
+
+template <int K>
+__device__ __forceinline__ FastDec make_fast_dec(const pc_batch& b) {
+    FastDec d;
+    const float cx = ldexpf(b.size[0], -10 * K), cy = ldexpf(b.size[1], -10 * K);
+    const float cz = ldexpf(b.size[2], -10 * K);
+    d.mn = f2_pack(b.min[0], b.min[1]);
+    d.cell = f2_pack(cx, cy);
+    d.nb = f2_pack(-ldexpf(cx, 23), -ldexpf(cy, K == 1 ? 13 : 23));
+    d.mnz = b.min[2];
+    d.cellz = cz;
+    d.nbz = -ldexpf(cz, 23);
+    return d;
+}
+
+// Clip coordinates of one point of a certified batch: (cx, cy) as a packed
+// pair, and cw.
+template <int K>
+__device__ __forceinline__ void fast_clip(const FastView& fv, const FastDec& d, uint32_t a,
+                                          uint32_t b, f2_t& cxy, float& cw) {
+    uint32_t fx, fy, fz;
+    if (K == 1) {
+        fx = (a & 0x3FFu) | 0x4B000000u;
+        fy = (a & 0xFFC00u) | 0x46000000u;
+        fz = ((a >> 20) & 0x3FFu) | 0x4B000000u;
+    } else {
+        uint32_t qx, qy, qz;
+        decode_q<2>(a, b, 0u, qx, qy, qz);
+        fx = qx | 0x4B000000u;
+        fy = qy | 0x4B000000u;
+        fz = qz | 0x4B000000u;
+    }
+    const f2_t xy = f2_add(d.mn, f2_fma_rn(f2_pack(__uint_as_float(fx), __uint_as_float(fy)),
+                                           d.cell, d.nb));
+    const float z = __fadd_rn(d.mnz, __fmaf_rn(__uint_as_float(fz), d.cellz, d.nbz));
+    float x, y;
+    f2_unpack(xy, x, y);
+    const f2_t zero = f2_pack(0.0f, 0.0f);
+    const f2_t px = f2_fma_rn(fv.m01, f2_pack(x, x), zero);
+    const f2_t py = f2_fma_rn(fv.m45, f2_pack(y, y), zero);
+    const f2_t pz = f2_fma_rn(fv.m89, f2_pack(z, z), zero);
+    cxy = f2_add(f2_add(f2_add(px, py), pz), fv.m1213);
+    float w0, w1;
+    f2_unpack(f2_fma_rn(fv.m37, xy, zero), w0, w1);
+    cw = __fadd_rn(__fadd_rn(__fadd_rn(w0, w1), __fmul_rn(fv.m11, z)), fv.m15);
+}
+
+// One lane's group of 4 points of a certified batch.
+template <int K, bool STREAM>
+__device__ __forceinline__ uint32_t raster_group_fast(const CloudView& c, const FastView& fv,
+                                                      const FastDec& d, uint32_t g,
+                                                      const Scratch& s) {
+    const uint4 q1 = ld_words<STREAM>(c.w1 + g);
+    uint4 q2 = make_uint4(0, 0, 0, 0);
+    if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
+    const uint32_t wa[4] = {q1.x, q1.y, q1.z, q1.w};
+    const uint32_t wb[4] = {q2.x, q2.y, q2.z, q2.w};
+    f2_t cxy[4];
+    float cw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fast_clip<K>(fv, d, wa[j], wb[j], cxy[j], cw[j]);
+    const f2_t half = f2_pack(0.5f, 0.5f);
+    const f2_t clo = f2_pack(0.5f - 0x1.0p-21f, 0.5f - 0x1.0p-21f);
+    const f2_t chi = f2_pack(0.5f + 0x1.0p-21f, 0.5f + 0x1.0p-21f);
+    const f2_t magic = f2_pack(8388608.0f, 8388608.0f);
+    uint32_t bx[4], by[4];
+    bool slow = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float r = rcp_approx(cw[j]);
+        const f2_t q = f2_mul(cxy[j], f2_pack(r, r));
+        const f2_t blo = f2_fma_rd(f2_fma_rn(q, half, clo), fv.wh, magic);
+        const f2_t bhi = f2_fma_rd(f2_fma_rn(q, half, chi), fv.wh, magic);
+        slow |= blo != bhi;
+        bx[j] = (uint32_t)blo;
+        by[j] = (uint32_t)(blo >> 32);
+    }
+    if (slow) {
+        // a bracket did not settle: the definition for all four (rare)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float cx, cy;
+            f2_unpack(cxy[j], cx, cy);
+            bx[j] = exact_floor_bits(cx, cw[j], __uint_as_float((uint32_t)fv.wh));
+            by[j] = exact_floor_bits(cy, cw[j], __uint_as_float((uint32_t)(fv.wh >> 32)));
+        }
+    }
+    uint32_t pix[4], w[4], lim[4];
+    const uint32_t* vis_hi = reinterpret_cast<const uint32_t*>(fv.vis) + 1;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        pix[j] = (by[j] - 0x4B000000u) * fv.width + (bx[j] - 0x4B000000u);
+        w[j] = __float_as_uint(cw[j]);
+        // the certificate puts every pixel inside the view; an index outside it
+        // is reported and skipped (lim 0: no w > 0 passes)
+        const bool in = pix[j] < fv.npix;
+        bad |= !in;
+        lim[j] = in ? vis_hi[2ull * pix[j]] : 0u;
+    }
+    if (bad) raise_error(s, E_PIXEL_RANGE, g);
+    bool need = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) need |= w[j] <= lim[j];
+    if (!need) return 0;
+    uint32_t n_atom = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (w[j] <= lim[j]) {
+            atomicMin(fv.vis + pix[j], ((unsigned long long)w[j] << 32) | (g + j));
+            ++n_atom;
+            if (j < 3 && pix[j + 1] == pix[j]) lim[j + 1] = min(lim[j + 1], w[j] - 1u);
+        }
+    }
+    return n_atom;
+}
+
+// Points [p0, p1) of a certified batch at precision K (1 or 2): whole groups
+// of 4 take the fast path, the groups of a ragged first or last step the
+// general one.
+template <int K, bool STREAM>
+__device__ __forceinline__ uint32_t segment_fast(const CloudView& c, const ViewConst& vc,
+                                                 const FastView& fv, const pc_batch& bt,
+                                                 uint32_t p0, uint32_t p1, uint32_t lane,
+                                                 const Scratch& s) {
+    uint32_t n_atom = 0;
+    uint32_t base = p0 & ~3u;
+    if (lane == 0 && p1 > base) {
+        const uint32_t bytes = ((p1 - base) * 4u + 15u) & ~15u;
+        prefetch_l2(c.w1 + base, bytes);
+        if (K >= 2) prefetch_l2(c.w2 + base, bytes);
+    }
+    if (base != p0 && base < p1) {
+        const uint32_t g = base + 4u * lane;
+        if (g < p1) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
+            n_atom += raster_group<K, STREAM, true>(c, vc, make_dec_const(bt, K), g, valid);
+        }
+        base += 128u;
+    }
+    {
+        const FastDec d = make_fast_dec<K>(bt);
+        for (; base + 128u <= p1; base += 128u)
+            n_atom += raster_group_fast<K, STREAM>(c, fv, d, base + 4u * lane, s);
+    }
+    if (base < p1) {
+        const uint32_t g = base + 4u * lane;
+        if (g < p1) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j < p1) << j;
+            n_atom += raster_group<K, STREAM, true>(c, vc, make_dec_const(bt, K), g, valid);
+        }
+    }
+    return n_atom;
+}
+
 constexpr int kRasterThreads = 256;
 
 __device__ __forceinline__ bool next_entry(const Scratch& s, uint32_t n_entries, uint32_t lane,
@@ -813,10 +1084,15 @@ __device__ __forceinline__ bool next_entry(const Scratch& s, uint32_t n_entries,
     return true;
 }
 
+// One segment for one view at its precision k; certified batches (fast) at
+// k <= 2 take the fast path.
 template <bool STREAM>
 __device__ __forceinline__ uint32_t segment_k(const CloudView& c, const ViewConst& vc,
-                                              const pc_batch& bt, int k, uint32_t p0, uint32_t p1,
-                                              uint32_t lane) {
+                                              const FastView& fv, const pc_batch& bt, int k,
+                                              bool fast, uint32_t p0, uint32_t p1,
+                                              uint32_t lane, const Scratch& s) {
+    if (fast && k == 1) return segment_fast<1, STREAM>(c, vc, fv, bt, p0, p1, lane, s);
+    if (fast && k == 2) return segment_fast<2, STREAM>(c, vc, fv, bt, p0, p1, lane, s);
     const DecConst d = make_dec_const(bt, k);
     if (k == 1) return segment<1, STREAM>(c, vc, d, p0, p1, lane);
     if (k == 2) return segment<2, STREAM>(c, vc, d, p0, p1, lane);
@@ -836,6 +1112,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster1(CloudView c, ViewTab
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n_entries = s.counters[C_ENTRIES];
     const ViewConst vc = make_view_const(vt.v[0]);
+    const FastView fv = make_fast_view(vt.v[0]);
     uint32_t n_atom = 0;
     DrawEntry e;
     while (next_entry(s, n_entries, lane, e)) {
@@ -845,7 +1122,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster1(CloudView c, ViewTab
         }
         const pc_batch bt = c.batches[e.batch];
         const uint32_t p0 = bt.first + e.seg_first;
-        n_atom += segment_k<true>(c, vc, bt, (int)(e.kcodes & 3u), p0, p0 + e.seg_count, lane);
+        n_atom += segment_k<true>(c, vc, fv, bt, (int)(e.kcodes & 3u), e.fast_mask & 1u, p0,
+                                  p0 + e.seg_count, lane, s);
     }
     flush_atomics(s, view_base, n_atom, lane);
 }
@@ -871,8 +1149,10 @@ __global__ void __launch_bounds__(kRasterThreads) k_rasterN(CloudView c, ViewTab
         for (uint32_t mm = e.view_mask; mm; mm &= mm - 1) {
             const uint32_t v = __ffs(mm) - 1;
             const ViewConst vc = make_view_const(vt.v[v]);
-            const uint32_t n = segment_k<false>(c, vc, bt, (int)((e.kcodes >> (2 * v)) & 3u),
-                                                p0, p0 + e.seg_count, lane);
+            const FastView fv = make_fast_view(vt.v[v]);
+            const uint32_t n = segment_k<false>(c, vc, fv, bt, (int)((e.kcodes >> (2 * v)) & 3u),
+                                                (e.fast_mask >> v) & 1u, p0, p0 + e.seg_count,
+                                                lane, s);
             const uint32_t t = __reduce_add_sync(FULL, n);
             if (lane == 0 && t) atomicAdd(&sh_atom[v], t);
         }
@@ -1166,6 +1446,7 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
     const uint64_t npix = (uint64_t)vp.width * vp.height;
     const bool dilate = (vp.flags & PC_VIEW_DILATE) != 0;
     const uint32_t mode = vp.accum ? hqs_mode(vp.flags) : 0u;
+    const unsigned long long empty = empty_key(vp.flags);
     if (!dilate && !mode) {
         // plain resolve, 4 pixels per thread: two 16-byte key loads, four
         // independent colour gathers, one 16-byte store (vis and rgba are
@@ -1181,7 +1462,7 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 col[j] = 0u;
-                if (key[j] != ~0ull) {
+                if (key[j] != empty) {
                     const uint32_t idx = (uint32_t)key[j];
                     if (idx < c.n_points) col[j] = __ldg(c.color + idx);
                     else raise_error(s, E_INDEX_RANGE, idx);
@@ -1193,7 +1474,7 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
              p += (uint64_t)gridDim.x * blockDim.x) {
             const unsigned long long key = vp.vis[p];
             uint32_t out = 0u;
-            if (key != ~0ull) {
+            if (key != empty) {
                 const uint32_t idx = (uint32_t)key;
                 if (idx < c.n_points) out = c.color[idx];
                 else raise_error(s, E_INDEX_RANGE, idx);
@@ -1224,7 +1505,7 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
                 }
         }
         uint32_t out = 0u;
-        if (mode && key != ~0ull) {
+        if (mode && key != empty) {
             // Sec. 3.6: per-channel average of the sums, rounded down
             uint32_t r, g, b, n;
             const ulonglong2* two = reinterpret_cast<const ulonglong2*>(vp.accum);   // two-word sums
@@ -1247,13 +1528,31 @@ __global__ void k_resolve(CloudView c, ViewTable vt, Scratch s) {
                 if (n > kHqsMaxCount) raise_error(s, E_HQS_OVERFLOW, (uint32_t)at);
             }
             if (n) out = (r / n) | ((g / n) << 8) | ((b / n) << 16) | 0xFF000000u;
-        } else if (key != ~0ull) {
+        } else if (key != empty) {
             const uint32_t idx = (uint32_t)key;
             if (idx < c.n_points) out = c.color[idx];
             else raise_error(s, E_INDEX_RANGE, idx);
         }
         vp.rgba[p] = out;
     }
+}
+
+// ---- k_merge_min: element-wise minimum of two visibility buffers ------------------
+//
+// Shards of one frame (disjoint batch ranges, Sec. 3.2) merge exactly: the
+// minimum over (depth bits << 32 | index) keys is associative and commutative.
+// 16-byte loads and stores (both buffers 16-byte aligned); the odd last key alone.
+__global__ void k_merge_min(unsigned long long* dst, const unsigned long long* src, uint64_t n) {
+    ulonglong2* d2 = reinterpret_cast<ulonglong2*>(dst);
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(src);
+    const uint64_t n2 = n / 2;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const ulonglong2 a = d2[i], b = s2[i];
+        d2[i] = make_ulonglong2(a.x < b.x ? a.x : b.x, a.y < b.y ? a.y : b.y);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+        dst[n - 1] = dst[n - 1] < src[n - 1] ? dst[n - 1] : src[n - 1];
 }
 
 int g_num_sms = 0;
@@ -1348,6 +1647,16 @@ cudaError_t launch_shade(const CloudView& c, const ViewTable& vt, uint32_t view_
     e = launch_shade_kernel<0>(c, vt, view_base, s, threads, packed, st);
     *launched = 2;
     return e;
+}
+
+cudaError_t launch_merge_min(uint64_t* dst, const uint64_t* src, uint64_t n, cudaStream_t st) {
+    const int threads = 256;
+    uint64_t blocks = (n / 2 + threads - 1) / threads;
+    blocks = blocks < 1 ? 1 : (blocks > (uint64_t)num_sms() * 8 ? (uint64_t)num_sms() * 8 : blocks);
+    k_merge_min<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<unsigned long long*>(dst),
+                                                      reinterpret_cast<const unsigned long long*>(src),
+                                                      n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(const CloudView& c, const ViewTable& vt, Scratch s, cudaStream_t st) {

@@ -24,6 +24,7 @@ namespace pcr {
 namespace serve_detail {
 
 constexpr uint32_t kMaxViewsPerRequest = 32;
+constexpr int32_t kMaxPollMs = 60000;   // the longest single wait of pc_poll
 
 enum ReqState { R_QUEUED = 0, R_RUNNING = 1, R_DONE = 2 };
 
@@ -151,12 +152,13 @@ void retire(ServeState& s, Lane& lane) {
 }
 
 // Pick the next group from the queue (called with s.mu held): the oldest
-// request that fits the pool decides the cloud; later requests of the same
-// cloud join while views and memory allow. A request that has waited more
+// request that fits the pool decides the cloud, and that cloud's views per
+// launch the group's size; later requests of the same cloud join while views
+// and memory allow. A request that has waited more
 // than 200 ms blocks everything behind it, so large requests cannot starve.
 bool next_group(ServeState& s, std::vector<Request*>& group) {
     group.clear();
-    const uint32_t maxv = s.ctx->views_per_launch();
+    uint32_t maxv = kMaxViewsPerLaunch;   // set by the group's cloud
     uint32_t nviews = 0;
     const double now = s.ctx->now_ms();
     for (auto it = s.queue.begin(); it != s.queue.end();) {
@@ -183,6 +185,7 @@ bool next_group(ServeState& s, std::vector<Request*>& group) {
                 o += round_up(npix * 8) + round_up(npix * 4);
             }
         }
+        if (group.empty()) maxv = s.ctx->views_per_launch(*r->cloud);
         group.push_back(r);
         nviews += (uint32_t)r->views.size();
         it = s.queue.erase(it);
@@ -360,16 +363,19 @@ pc_status pc_poll(pc_ctx* h, pc_ticket ticket, int32_t timeout_ms, pc_result* ou
     ServeState* sp = ctx->serve.load();
     if (!sp) return PC_ENOTFOUND;
     ServeState& s = *sp;
+    if (timeout_ms < 0) {
+        ctx->fail_msg("pc_poll: timeout %d ms is negative (0..%d)", timeout_ms, kMaxPollMs);
+        return PC_EINVAL;
+    }
     std::unique_lock<std::mutex> lk(s.mu);
     auto it = s.reqs.find(ticket);
     if (it == s.reqs.end()) return PC_ENOTFOUND;
     Request* r = it->second.get();
     auto done = [&] { return r->state == R_DONE; };
-    if (timeout_ms < 0) {
-        while (!done()) s.cv_done.wait_for(lk, std::chrono::milliseconds(100));
-    } else if (!done()) {
-        s.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
-    }
+    // one bounded wait: a request whose stream never finishes (held by a
+    // callback, a hung kernel) costs the caller at most kMaxPollMs
+    if (!done())
+        s.cv_done.wait_for(lk, std::chrono::milliseconds(std::min(timeout_ms, kMaxPollMs)), done);
     if (!done()) return PC_ETIMEDOUT;
     std::memset(out, 0, sizeof *out);
     out->status = r->status;

@@ -76,7 +76,7 @@ def test_full_size_frames_bit_exact(cuda_lib):
         own = ctx.framebuffers([v0])
         t2 = pcr.pc_submit(ctx.h, cloud, [v0], [(own[0][0].data_ptr(), own[0][1].data_ptr())])
         for t in (t1, t2):
-            rc, res = pcr.pc_poll(ctx.h, t, 120_000)
+            rc, res = pcr.pc_poll(ctx.h, t, 60_000)
             assert rc == pcr.PC_OK and res["status"] == pcr.PC_OK
         expect = O.resolve(overview_vis, enc.color)
         assert np.array_equal(pcr.pc_poll(ctx.h, t1, 0)[1]["images"][0], expect)

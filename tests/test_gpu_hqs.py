@@ -253,5 +253,5 @@ def test_empty_view_and_noalloc_refusal(world):
     vis2 = torch.empty(64 * 64, dtype=torch.int64, device=dev)
     img2 = torch.empty(64 * 64, dtype=torch.int32, device=dev)
     assert L.pc_render_noalloc(b.data_ptr(), 1, *(w.data_ptr(),) * 4, 4, ctypes.byref(v),
-                               vis2.data_ptr(), img2.data_ptr(), 512.0,
+                               vis2.data_ptr(), img2.data_ptr(), 512.0, None,
                                torch.cuda.current_stream().cuda_stream) == pcr.PC_ENOTSUP

@@ -115,6 +115,28 @@ def test_poll_never_hangs_and_times_out(world):
         pcr.pc_release_ticket(ctx.h, 987654321)
 
 
+def test_poll_wait_is_bounded(world):
+    """pc_poll has no unbounded wait: a negative timeout is refused, and a
+    request still queued behind others answers PC_ETIMEDOUT after about the
+    timeout it was given."""
+    ctx, (c1, p1), _ = world
+    views = [pcr.make_view(S.random_view(p1, 80 + i, 2048, 2048, seed=4), 2048, 2048,
+                           pcr.PC_VIEW_CULL | pcr.PC_VIEW_NO_EARLY_DEPTH) for i in range(8)]
+    tickets = [pcr.pc_submit(ctx.h, c1, views) for _ in range(8)]
+    with pytest.raises(pcr.PCError) as e:
+        pcr.pc_poll(ctx.h, tickets[-1], -1)
+    assert e.value.status == pcr.PC_EINVAL
+    t0 = time.perf_counter()
+    rc, _ = pcr.pc_poll(ctx.h, tickets[-1], 25)
+    dt = time.perf_counter() - t0
+    if rc == pcr.PC_ETIMEDOUT:
+        assert 0.02 <= dt < 0.5
+    for t in tickets:
+        rc, res = pcr.pc_poll(ctx.h, t, 20000)
+        assert rc == pcr.PC_OK and res["status"] == pcr.PC_OK
+        pcr.pc_release_ticket(ctx.h, t)
+
+
 def test_admission_refused_when_it_can_never_fit(cuda_lib):
     ctx = pcr.Context(0, serve_pool_bytes=8 << 20)
     try:
