@@ -57,13 +57,17 @@ def parse():
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--seed", type=int, default=3)
-    ap.add_argument("--cpu-sample", type=float, default=8e6)
+    ap.add_argument("--cpu-sample", type=float, default=8e6,
+                    help="points per step of the reference arm (the oracle alone)")
+    ap.add_argument("--cpu-single-points", type=float, default=5e7,
+                    help="points of the one-core oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=240)
-    ap.add_argument("--serve-rate", type=float, default=4000.0,
-                    help="Poisson arrival rate of requests per second (offered load)")
+    ap.add_argument("--serve-rate", type=float, default=0.0,
+                    help="Poisson arrival rate of the saturating runs in requests per second; "
+                         "0 submits every request at once (the capacity)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-lod", action="store_true")
     ap.add_argument("--no-multiview", action="store_true")
@@ -183,6 +187,42 @@ def cpu_baseline(args, params, m, sample_points, threads=None):
     return pps, cores, desc, enc, v
 
 
+def full_frame_oracle(args, pcr, ctx, cloud, m):
+    """The CPU oracle on the whole frame the GPU renders: the encoded cloud
+    copied back from the device, the geometry pass with culling threaded over
+    all host cores, one frame timed; then one core over a stated sample of the
+    same cloud."""
+    import oracle
+    info = pcr.pc_cloud_get_info(ctx.h, cloud)
+    t0 = time.perf_counter()
+    batches, w1, w2, w3, col = pcr.pc_cloud_download(ctx.h, cloud)
+    t_dl = time.perf_counter() - t0
+    enc = oracle.Encoded(batches, w1, w2, w3, col, None)
+    v = oracle.make_view(m, args.width, args.height, cull=True)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    _, st = oracle.render_threaded(enc, v, threads=cores)
+    dt = time.perf_counter() - t0
+    # one core: the first batches of the same cloud, about 2 s of work
+    nb = max(1, min(len(batches), int(args.cpu_single_points) // 10240))
+    part = oracle.Encoded(batches[:nb], w1, w2, w3, col, None)
+    t1 = time.perf_counter()
+    _, st1 = oracle.render_threaded(part, v, threads=1)
+    dt1 = time.perf_counter() - t1
+    del enc, part, batches, w1, w2, w3, col
+    return {"value": st["points_processed"] / dt / 1e9, "unit": "Gpoints/s", "cores": cores,
+            "kind": "oracle", "points": int(info.n_points),
+            "ms_per_frame": dt * 1e3,
+            "sample": (f"the whole frame: all {int(info.n_points):,} points of the cloud "
+                       f"({st['points_processed']:,} processed after culling), copied back "
+                       f"from the device in {t_dl:.1f} s, oracle geometry pass threaded on "
+                       f"{cores} host cores, one frame"),
+            "single_thread": {"value": st1["points_processed"] / dt1 / 1e9,
+                              "points": int(st1["points_processed"]),
+                              "sample": f"the first {nb:,} batches of the same cloud, same "
+                                        f"camera, one core"}}
+
+
 def serving_bench(args, pcr, ctx, clouds):
     """Poisson stream of view requests over resident clouds, served with
     multi-view batching (views per launch tuned per cloud) and with one view
@@ -215,12 +255,14 @@ def serving_bench(args, pcr, ctx, clouds):
     tuned = {}
     for ci, (cloud, params, name) in enumerate(clouds):
         sample = [pcr.make_view(pcsynth.random_view(params, 900 + k, 1920, 1080, seed=args.seed),
-                                1920, 1080, pcr.PC_VIEW_CULL) for k in range(8)]
+                                1920, 1080, pcr.PC_VIEW_CULL) for k in range(16)]
         tuned[name] = pcr.pc_autotune(ctx.h, cloud, sample)
 
-    def run(vpl, rate):
+    def run(vpl, rate, subset=None, verify=False):
+        sub = reqs if subset is None else [reqs[i] for i in subset]
+        sub_gaps = gaps if subset is None else [gaps[i] for i in subset]
         pcr.pc_set_views_per_launch(ctx.h, vpl)
-        tickets, results = [], [None] * len(reqs)
+        tickets, results = [], [None] * len(sub)
         lock = threading.Condition()
         done_submitting = [False]
 
@@ -233,13 +275,16 @@ def serving_bench(args, pcr, ctx, clouds):
                     if k >= len(tickets):
                         return
                     tk = tickets[k]
-                rc, res = pcr.pc_poll(ctx.h, tk, 60000)
+                rc, res = pcr.pc_poll(ctx.h, tk, 60000, copy_images=verify)
                 if rc != pcr.PC_OK:
                     raise RuntimeError("serving request did not finish within 60 s")
-                h = hashlib.sha256()
-                for img in res["images"]:
-                    h.update(img.tobytes())
-                results[k] = (res["t_submit_ms"], res["t_done_ms"], h.hexdigest(), res["status"])
+                digest = None
+                if verify:   # untimed runs only: hashing images in Python is slow
+                    h = hashlib.sha256()
+                    for img in res["images"]:
+                        h.update(img.tobytes())
+                    digest = h.hexdigest()
+                results[k] = (res["t_submit_ms"], res["t_done_ms"], digest, res["status"])
                 pcr.pc_release_ticket(ctx.h, tk)
                 k += 1
 
@@ -247,7 +292,7 @@ def serving_bench(args, pcr, ctx, clouds):
         th.start()
         t0 = time.perf_counter()
         ta = 0.0
-        for gap, (_, cloud, views) in zip(gaps, reqs):
+        for gap, (_, cloud, views) in zip(sub_gaps, sub):
             ta += gap / rate
             d = ta - (time.perf_counter() - t0)
             if d > 0:
@@ -270,41 +315,60 @@ def serving_bench(args, pcr, ctx, clouds):
         t_sub = min(r[0] for r in results)
         t_done = max(r[1] for r in results)
         lat = np.array([r[1] - r[0] for r in results])
-        out = {"offered_req_per_s": rate, "views_per_s": nviews / ((t_done - t_sub) / 1e3),
+        sub_views = sum(len(v) for _, _, v in sub)
+        out = {"offered_req_per_s": rate if rate != float("inf") else "all at once",
+               "views_per_s": sub_views / ((t_done - t_sub) / 1e3),
                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                "ok": all(r[3] == pcr.PC_OK for r in results), "per_cloud": {}}
         for ci, (_, _, name) in enumerate(clouds):
-            sel = np.array([r[0] == ci for r in reqs])
+            sel = np.array([r[0] == ci for r in sub])
             if sel.any():
                 out["per_cloud"][name] = {"requests": int(sel.sum()),
                                           "p50_ms": float(np.percentile(lat[sel], 50)),
                                           "p99_ms": float(np.percentile(lat[sel], 99))}
         return out, [r[2] for r in results]
 
-    saturate = args.serve_rate
-    run(0, saturate)   # warm-up: streams, pools, graphs
-    batched, hb = run(0, saturate)       # per-cloud tuned views per launch
-    single, hs = run(1, saturate)
+    saturate = args.serve_rate if args.serve_rate > 0 else float("inf")
+    # the images of every request, batched and one view per launch, must be the
+    # same: checked in untimed runs that hash each image
+    _, hb = run(0, saturate, verify=True)   # also the warm-up: streams, pools, graphs
+    _, hs = run(1, saturate, verify=True)
+    same = hb == hs
+    batched, _ = run(0, saturate)       # per-cloud tuned views per launch
+    single, _ = run(1, saturate)
     capacity_req = single["views_per_s"] / views_per_req
     loads = {}
-    same = hb == hs
     for frac in (0.5, 0.9):
-        b, hb2 = run(0, frac * capacity_req)
-        s1, hs2 = run(1, frac * capacity_req)
-        same = same and hb2 == hb and hs2 == hb
+        b, _ = run(0, frac * capacity_req)
+        s1, _ = run(1, frac * capacity_req)
         loads[f"{int(frac * 100)}pct_of_one_view_capacity"] = {"batched": b, "one_view_per_launch": s1}
+    # each cloud's requests alone, at a saturating rate: views/s batched vs one
+    # view per launch for that cloud
+    alone = {}
+    for ci, (_, _, name) in enumerate(clouds):
+        idx = [i for i, r in enumerate(reqs) if r[0] == ci]
+        if not idx:
+            continue
+        b, _ = run(0, saturate, idx)
+        s1, _ = run(1, saturate, idx)
+        alone[name] = {"requests": len(idx), "views_per_s_batched": b["views_per_s"],
+                       "views_per_s_one_view_per_launch": s1["views_per_s"],
+                       "speedup": b["views_per_s"] / s1["views_per_s"],
+                       "p50_ms_batched": b["p50_ms"], "p50_ms_one_view_per_launch": s1["p50_ms"]}
     pcr.pc_set_views_per_launch(ctx.h, 0)
     return {"requests": len(reqs), "views": nviews,
             "clouds": [c[2] for c in clouds],
             "resolutions": "1280x720 / 1920x1080 / 3840x2160 / stereo 2x2016x2240, uniform",
             "tuned": tuned,
-            "saturating_offered_req_per_s": saturate,
+            "saturating_offered_req_per_s": args.serve_rate if args.serve_rate > 0 else "all at once",
             "views_per_s": batched["views_per_s"], "p50_ms": batched["p50_ms"],
             "p99_ms": batched["p99_ms"], "saturated": batched,
             "one_view_per_launch": single,
             "speedup_vs_one_view_per_launch": batched["views_per_s"] / single["views_per_s"],
-            "sustainable": loads,
-            "identical_bits": same, "all_ok": batched["ok"] and single["ok"]}
+            "sustainable": loads, "each_cloud_alone": alone,
+            "identical_bits": same, "identical_bits_checked": "every image of every request, "
+            "batched vs one view per launch, in untimed runs",
+            "all_ok": batched["ok"] and single["ok"]}
 
 
 def small_configs_bench(args, pcr, torch, ctx):
@@ -502,7 +566,12 @@ def hqs_bench(args, pcr, torch, ctx, cloud, m, plain_ms):
             ctx.render(cloud, [v], fbs)
         t = pcr.pc_timing_end(ctx.h)
         f = max(1, t.frames)
+        info = pcr.pc_cloud_get_info(ctx.h, cloud)
+        layout = name
+        if flag == pcr.PC_VIEW_HQS_PACKED and info.n_points > 256 * W * H:
+            layout = "two_word (more than 256 points per pixel: the library's rule)"
         out[name] = {"ms_per_frame": ms, "frames": k, "cost_vs_plain": ms / plain_ms,
+                     "layout_used": layout,
                      "passes_ms": {"clear": t.ms_clear / f, "cull": t.ms_cull / f,
                                    "depth": t.ms_raster / f, "shade": t.ms_shade / f,
                                    "resolve": t.ms_resolve / f},
@@ -801,10 +870,8 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        pps, cores, desc, _, _ = cpu_baseline(args, params, m, args.cpu_sample)
-        pps1, _, desc1, _, _ = cpu_baseline(args, params, m, min(args.cpu_sample, 2e6), threads=1)
-        cpu = {"value": pps / 1e9, "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
-               "sample": desc, "single_thread": {"value": pps1 / 1e9, "sample": desc1}}
+        cpu = full_frame_oracle(args, pcr, ctx, cloud, m)
+        log(args, f"cpu baseline: {cpu}")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world,

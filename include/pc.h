@@ -218,7 +218,10 @@ pc_status pc_lod_encode(const float* xyz, const uint32_t* rgba, uint64_t n,
                                               pass with two atomics per point, so the image is
                                               exact in every case (the second pass returns at
                                               once when no pixel overflowed). Set alone or with
-                                              PC_VIEW_HQS; takes precedence */
+                                              PC_VIEW_HQS; takes precedence, except for a cloud
+                                              of more than 256 points per pixel of the view,
+                                              where two-word sums are used (faster there; the
+                                              image is the same) */
 
 typedef struct {
     float    view_proj[16];   /* world -> clip, column-major; finite (a NaN or an infinity

@@ -481,17 +481,17 @@ def pc_submit(ctx: int, cloud: int, views, fbs=None) -> int:
     return out.value
 
 
-def pc_poll(ctx: int, ticket: int, timeout_ms: int = 10000):
+def pc_poll(ctx: int, ticket: int, timeout_ms: int = 10000, copy_images: bool = True):
     """Returns (status, result) — status PC_OK or PC_ETIMEDOUT; result holds
-    numpy copies of the images when PC_OK. timeout_ms: 0..60000 (larger values
-    wait 60 s; negative ones raise)."""
+    numpy copies of the images when PC_OK (none with copy_images=False).
+    timeout_ms: 0..60000 (larger values wait 60 s; negative ones raise)."""
     r = pc_result()
     rc = lib().pc_poll(ctx, ticket, timeout_ms, ctypes.byref(r))
     if rc == PC_ETIMEDOUT:
         return rc, None
     _check(ctx, rc)
     imgs = []
-    for v in range(r.nviews if r.rgba else 0):
+    for v in range(r.nviews if (r.rgba and copy_images) else 0):
         n = r.widths[v] * r.heights[v]
         imgs.append(np.ctypeslib.as_array(r.rgba[v], shape=(n,)).copy())
     return rc, {"status": r.status, "images": imgs, "t_submit_ms": r.t_submit_ms,

@@ -333,6 +333,19 @@ pc_status Ctx::render(const Cloud& cl, const pc_view* views, uint32_t nviews,
             return PC_EINVAL;
         }
     }
+    // PC_VIEW_HQS_PACKED is a preference: with more than 256 points of the
+    // cloud per pixel of a view, many pixels pass 1023 points and the packed
+    // sums' second pass costs more than two-word sums; both are exact, so the
+    // image is the same
+    std::vector<pc_view> eff;
+    for (uint32_t v = 0; v < nviews; ++v) {
+        const uint64_t npix = (uint64_t)views[v].width * views[v].height;
+        if ((views[v].flags & PC_VIEW_HQS_PACKED) && cl.n_points > 256ull * npix) {
+            if (eff.empty()) eff.assign(views, views + nviews);
+            eff[v].flags = (eff[v].flags & ~PC_VIEW_HQS_PACKED) | PC_VIEW_HQS;
+        }
+    }
+    if (!eff.empty()) views = eff.data();
     if (!slot) slot = slot_for(st);
     std::lock_guard<std::mutex> sg(slot->mu);
     const uint32_t maxv = views_per_launch(cl);   // one value for the whole call

@@ -47,7 +47,6 @@ enum : uint32_t {
     E_BATCH_RANGE = 2,     // batch outside the point buffers
     E_INDEX_RANGE = 3,     // visibility key with an index outside the cloud
     E_HQS_OVERFLOW = 4,    // a pixel's colour sums exceeded their field width
-    E_PIXEL_RANGE = 5,     // a certified batch produced a pixel outside its view
 };
 
 // One view as the kernels see it (passed by value in a ViewTable).

@@ -928,11 +928,11 @@ __device__ __forceinline__ FastDec make_fast_dec(const pc_batch& b) {
     return d;
 }
 
-// Clip coordinates of one point of a certified batch: (cx, cy) as a packed
-// pair, and cw.
+// Decoded position of one point of a certified batch: (x, y) as a packed
+// pair, and z.
 template <int K>
-__device__ __forceinline__ void fast_clip(const FastView& fv, const FastDec& d, uint32_t a,
-                                          uint32_t b, f2_t& cxy, float& cw) {
+__device__ __forceinline__ void fast_decode(const FastDec& d, uint32_t a, uint32_t b, f2_t& xy,
+                                            float& z) {
     uint32_t fx, fy, fz;
     if (K == 1) {
         fx = (a & 0x3FFu) | 0x4B000000u;
@@ -945,9 +945,13 @@ __device__ __forceinline__ void fast_clip(const FastView& fv, const FastDec& d, 
         fy = qy | 0x4B000000u;
         fz = qz | 0x4B000000u;
     }
-    const f2_t xy = f2_add(d.mn, f2_fma_rn(f2_pack(__uint_as_float(fx), __uint_as_float(fy)),
-                                           d.cell, d.nb));
-    const float z = __fadd_rn(d.mnz, __fmaf_rn(__uint_as_float(fz), d.cellz, d.nbz));
+    xy = f2_add(d.mn, f2_fma_rn(f2_pack(__uint_as_float(fx), __uint_as_float(fy)), d.cell, d.nb));
+    z = __fadd_rn(d.mnz, __fmaf_rn(__uint_as_float(fz), d.cellz, d.nbz));
+}
+
+// Clip coordinates of a decoded point: (cx, cy) as a packed pair, and cw.
+__device__ __forceinline__ void fast_project(const FastView& fv, f2_t xy, float z, f2_t& cxy,
+                                             float& cw) {
     float x, y;
     f2_unpack(xy, x, y);
     const f2_t zero = f2_pack(0.0f, 0.0f);
@@ -960,36 +964,44 @@ __device__ __forceinline__ void fast_clip(const FastView& fv, const FastDec& d, 
     cw = __fadd_rn(__fadd_rn(__fadd_rn(w0, w1), __fmul_rn(fv.m11, z)), fv.m15);
 }
 
-// One lane's group of 4 points of a certified batch.
-template <int K, bool STREAM>
-__device__ __forceinline__ uint32_t raster_group_fast(const CloudView& c, const FastView& fv,
-                                                      const FastDec& d, uint32_t g,
-                                                      const Scratch& s) {
-    const uint4 q1 = ld_words<STREAM>(c.w1 + g);
-    uint4 q2 = make_uint4(0, 0, 0, 0);
-    if (K >= 2) q2 = ld_words<STREAM>(c.w2 + g);
-    const uint32_t wa[4] = {q1.x, q1.y, q1.z, q1.w};
-    const uint32_t wb[4] = {q2.x, q2.y, q2.z, q2.w};
+// Clip coordinates of one point of a certified batch from its words.
+template <int K>
+__device__ __forceinline__ void fast_clip(const FastView& fv, const FastDec& d, uint32_t a,
+                                          uint32_t b, f2_t& cxy, float& cw) {
+    f2_t xy;
+    float z;
+    fast_decode<K>(d, a, b, xy, z);
+    fast_project(fv, xy, z, cxy, cw);
+}
+
+// Floor bits of a point of a certified batch by the bracket (no Newton step);
+// false when the two ends differ and the IEEE-divide path must decide.
+__device__ __forceinline__ bool pixel_bracket(const FastView& fv, f2_t cxy, float cw,
+                                              uint32_t& bx, uint32_t& by) {
+    const float r = rcp_approx(cw);
+    const f2_t q = f2_mul(cxy, f2_pack(r, r));
+    const f2_t half = f2_pack(0.5f, 0.5f);
+    const f2_t blo = f2_fma_rd(f2_fma_rn(q, half, f2_pack(0.5f - 0x1.0p-21f, 0.5f - 0x1.0p-21f)),
+                               fv.wh, f2_pack(8388608.0f, 8388608.0f));
+    const f2_t bhi = f2_fma_rd(f2_fma_rn(q, half, f2_pack(0.5f + 0x1.0p-21f, 0.5f + 0x1.0p-21f)),
+                               fv.wh, f2_pack(8388608.0f, 8388608.0f));
+    bx = (uint32_t)blo;
+    by = (uint32_t)(blo >> 32);
+    return blo == bhi;
+}
+
+// A lane's group of 4 decoded points of a certified batch in one view:
+// projection, pixel, early-depth reads and atomics.
+__device__ __forceinline__ uint32_t raster_decoded(const FastView& fv, const f2_t (&xy)[4],
+                                                   const float (&z)[4], uint32_t g) {
     f2_t cxy[4];
     float cw[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) fast_clip<K>(fv, d, wa[j], wb[j], cxy[j], cw[j]);
-    const f2_t half = f2_pack(0.5f, 0.5f);
-    const f2_t clo = f2_pack(0.5f - 0x1.0p-21f, 0.5f - 0x1.0p-21f);
-    const f2_t chi = f2_pack(0.5f + 0x1.0p-21f, 0.5f + 0x1.0p-21f);
-    const f2_t magic = f2_pack(8388608.0f, 8388608.0f);
+    for (int j = 0; j < 4; ++j) fast_project(fv, xy[j], z[j], cxy[j], cw[j]);
     uint32_t bx[4], by[4];
     bool slow = false;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float r = rcp_approx(cw[j]);
-        const f2_t q = f2_mul(cxy[j], f2_pack(r, r));
-        const f2_t blo = f2_fma_rd(f2_fma_rn(q, half, clo), fv.wh, magic);
-        const f2_t bhi = f2_fma_rd(f2_fma_rn(q, half, chi), fv.wh, magic);
-        slow |= blo != bhi;
-        bx[j] = (uint32_t)blo;
-        by[j] = (uint32_t)(blo >> 32);
-    }
+    for (int j = 0; j < 4; ++j) slow |= !pixel_bracket(fv, cxy[j], cw[j], bx[j], by[j]);
     if (slow) {
         // a bracket did not settle: the definition for all four (rare)
 #pragma unroll
@@ -1002,18 +1014,14 @@ __device__ __forceinline__ uint32_t raster_group_fast(const CloudView& c, const 
     }
     uint32_t pix[4], w[4], lim[4];
     const uint32_t* vis_hi = reinterpret_cast<const uint32_t*>(fv.vis) + 1;
-    bool bad = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        pix[j] = (by[j] - 0x4B000000u) * fv.width + (bx[j] - 0x4B000000u);
+        // the certificate puts every pixel inside the view, so the clamp changes
+        // nothing; it only keeps every access inside the buffer
+        pix[j] = min((by[j] - 0x4B000000u) * fv.width + (bx[j] - 0x4B000000u), fv.npix - 1u);
         w[j] = __float_as_uint(cw[j]);
-        // the certificate puts every pixel inside the view; an index outside it
-        // is reported and skipped (lim 0: no w > 0 passes)
-        const bool in = pix[j] < fv.npix;
-        bad |= !in;
-        lim[j] = in ? vis_hi[2ull * pix[j]] : 0u;
+        lim[j] = vis_hi[2ull * pix[j]];
     }
-    if (bad) raise_error(s, E_PIXEL_RANGE, g);
     bool need = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) need |= w[j] <= lim[j];
@@ -1030,14 +1038,38 @@ __device__ __forceinline__ uint32_t raster_group_fast(const CloudView& c, const 
     return n_atom;
 }
 
+// Decode of a lane's group of 4 points from its words (k <= 2).
+template <int K>
+__device__ __forceinline__ void decode_group(const FastDec& d, const uint4& q1, const uint4& q2,
+                                             f2_t (&xy)[4], float (&z)[4]) {
+    fast_decode<K>(d, q1.x, q2.x, xy[0], z[0]);
+    fast_decode<K>(d, q1.y, q2.y, xy[1], z[1]);
+    fast_decode<K>(d, q1.z, q2.z, xy[2], z[2]);
+    fast_decode<K>(d, q1.w, q2.w, xy[3], z[3]);
+}
+
+// One lane's group of 4 points of a certified batch, its words given.
+template <int K>
+__device__ __forceinline__ uint32_t raster_group_fast(const FastView& fv, const FastDec& d,
+                                                      const uint4& q1, const uint4& q2,
+                                                      uint32_t g) {
+    f2_t xy[4];
+    float z[4];
+    decode_group<K>(d, q1, q2, xy, z);
+    return raster_decoded(fv, xy, z, g);
+}
+
 // Points [p0, p1) of a certified batch at precision K (1 or 2): whole groups
 // of 4 take the fast path, the groups of a ragged first or last step the
-// general one.
+// general one. A lane loads the words of its next step while it projects the
+// current one, so the load's latency hides behind that step's arithmetic. The
+// depth reads are not moved ahead: a read issued before the previous step's
+// atomics would miss their updates, and the extra atomics cost more than the
+// latency saved.
 template <int K, bool STREAM>
 __device__ __forceinline__ uint32_t segment_fast(const CloudView& c, const ViewConst& vc,
                                                  const FastView& fv, const pc_batch& bt,
-                                                 uint32_t p0, uint32_t p1, uint32_t lane,
-                                                 const Scratch& s) {
+                                                 uint32_t p0, uint32_t p1, uint32_t lane) {
     uint32_t n_atom = 0;
     uint32_t base = p0 & ~3u;
     if (lane == 0 && p1 > base) {
@@ -1055,10 +1087,20 @@ __device__ __forceinline__ uint32_t segment_fast(const CloudView& c, const ViewC
         }
         base += 128u;
     }
-    {
+    if (base + 128u <= p1) {
         const FastDec d = make_fast_dec<K>(bt);
-        for (; base + 128u <= p1; base += 128u)
-            n_atom += raster_group_fast<K, STREAM>(c, fv, d, base + 4u * lane, s);
+        uint4 n1 = ld_words<STREAM>(c.w1 + base + 4u * lane);
+        uint4 n2 = make_uint4(0, 0, 0, 0);
+        if (K >= 2) n2 = ld_words<STREAM>(c.w2 + base + 4u * lane);
+        for (; base + 128u <= p1; base += 128u) {
+            const uint32_t g = base + 4u * lane;
+            const uint4 q1 = n1, q2 = n2;
+            if (base + 256u <= p1) {
+                n1 = ld_words<STREAM>(c.w1 + g + 128u);
+                if (K >= 2) n2 = ld_words<STREAM>(c.w2 + g + 128u);
+            }
+            n_atom += raster_group_fast<K>(fv, d, q1, q2, g);
+        }
     }
     if (base < p1) {
         const uint32_t g = base + 4u * lane;
@@ -1070,6 +1112,74 @@ __device__ __forceinline__ uint32_t segment_fast(const CloudView& c, const ViewC
         }
     }
     return n_atom;
+}
+
+// Points [p0, p1) of a certified batch at precision K for every view in vmask
+// (each certified for the batch, each at precision K): the words of a step are
+// loaded and decoded once, then projected into each view (Sec. 3.7). The
+// decoded positions are the same for every view, since they depend on the
+// batch and k only. Atomics per view go to the block's counters.
+template <int K>
+__device__ __forceinline__ void segment_fast_views(const CloudView& c, const ViewTable& vt,
+                                                   uint32_t vmask, const pc_batch& bt,
+                                                   uint32_t p0, uint32_t p1, uint32_t lane,
+                                                   uint32_t* sh_atom) {
+    uint32_t base = p0 & ~3u;
+    if (lane == 0 && p1 > base) {
+        const uint32_t bytes = ((p1 - base) * 4u + 15u) & ~15u;
+        prefetch_l2(c.w1 + base, bytes);
+        if (K >= 2) prefetch_l2(c.w2 + base, bytes);
+    }
+    // the ragged first and last steps view by view on the general path
+    auto partial = [&](uint32_t g, uint32_t valid) {
+        for (uint32_t mm = vmask; mm; mm &= mm - 1) {
+            const uint32_t v = __ffs(mm) - 1;
+            const uint32_t n = raster_group<K, false, true>(c, make_view_const(vt.v[v]),
+                                                           make_dec_const(bt, K), g, valid);
+            if (n) atomicAdd(&sh_atom[v], n);
+        }
+    };
+    if (base != p0 && base < p1) {
+        const uint32_t g = base + 4u * lane;
+        if (g < p1) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
+            partial(g, valid);
+        }
+        base += 128u;
+    }
+    if (base + 128u <= p1) {
+        const FastDec d = make_fast_dec<K>(bt);
+        uint4 n1 = ld_words<true>(c.w1 + base + 4u * lane);
+        uint4 n2 = make_uint4(0, 0, 0, 0);
+        if (K >= 2) n2 = ld_words<true>(c.w2 + base + 4u * lane);
+        for (; base + 128u <= p1; base += 128u) {
+            const uint32_t g = base + 4u * lane;
+            const uint4 q1 = n1, q2 = n2;
+            if (base + 256u <= p1) {
+                n1 = ld_words<true>(c.w1 + g + 128u);
+                if (K >= 2) n2 = ld_words<true>(c.w2 + g + 128u);
+            }
+            f2_t xy[4];
+            float z[4];
+            decode_group<K>(d, q1, q2, xy, z);
+            for (uint32_t mm = vmask; mm; mm &= mm - 1) {
+                const uint32_t v = __ffs(mm) - 1;
+                const uint32_t n = raster_decoded(make_fast_view(vt.v[v]), xy, z, g);
+                if (n) atomicAdd(&sh_atom[v], n);
+            }
+        }
+    }
+    if (base < p1) {
+        const uint32_t g = base + 4u * lane;
+        if (g < p1) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j < p1) << j;
+            partial(g, valid);
+        }
+    }
 }
 
 constexpr int kRasterThreads = 256;
@@ -1090,9 +1200,9 @@ template <bool STREAM>
 __device__ __forceinline__ uint32_t segment_k(const CloudView& c, const ViewConst& vc,
                                               const FastView& fv, const pc_batch& bt, int k,
                                               bool fast, uint32_t p0, uint32_t p1,
-                                              uint32_t lane, const Scratch& s) {
-    if (fast && k == 1) return segment_fast<1, STREAM>(c, vc, fv, bt, p0, p1, lane, s);
-    if (fast && k == 2) return segment_fast<2, STREAM>(c, vc, fv, bt, p0, p1, lane, s);
+                                              uint32_t lane) {
+    if (fast && k == 1) return segment_fast<1, STREAM>(c, vc, fv, bt, p0, p1, lane);
+    if (fast && k == 2) return segment_fast<2, STREAM>(c, vc, fv, bt, p0, p1, lane);
     const DecConst d = make_dec_const(bt, k);
     if (k == 1) return segment<1, STREAM>(c, vc, d, p0, p1, lane);
     if (k == 2) return segment<2, STREAM>(c, vc, d, p0, p1, lane);
@@ -1106,8 +1216,10 @@ __device__ __forceinline__ void flush_atomics(const Scratch& s, uint32_t view, u
         atomicAdd(&s.stats[(uint64_t)view * S_COUNT + S_ATOMICS], (unsigned long long)t);
 }
 
-// One view per launch: persistent warps take draw-list segments.
-__global__ void __launch_bounds__(kRasterThreads) k_raster1(CloudView c, ViewTable vt,
+// One view per launch: persistent warps take draw-list segments. Five blocks
+// of 256 threads per SM (48 registers): the depth reads' latency is hidden by
+// other warps, and more warps hide more of it.
+__global__ void __launch_bounds__(kRasterThreads, 5) k_raster1(CloudView c, ViewTable vt,
                                                            uint32_t view_base, Scratch s) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t n_entries = s.counters[C_ENTRIES];
@@ -1123,15 +1235,17 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster1(CloudView c, ViewTab
         const pc_batch bt = c.batches[e.batch];
         const uint32_t p0 = bt.first + e.seg_first;
         n_atom += segment_k<true>(c, vc, fv, bt, (int)(e.kcodes & 3u), e.fast_mask & 1u, p0,
-                                  p0 + e.seg_count, lane, s);
+                                  p0 + e.seg_count, lane);
     }
     flush_atomics(s, view_base, n_atom, lane);
 }
 
-// Several views per launch (Sec. 3.7): a warp walks each segment once per view
-// that did not cull its batch; the first walk brings the words from HBM, the
-// others find them in cache. Every view decodes at its own precision.
-__global__ void __launch_bounds__(kRasterThreads) k_rasterN(CloudView c, ViewTable vt,
+// Several views per launch (Sec. 3.7): the views certified for a segment's
+// batch at one precision share its word loads and its decode (one walk of the
+// segment); the others walk it once each, finding the words in cache. Every
+// view keeps its own culling and precision, so each image is the one-view
+// image bit for bit.
+__global__ void __launch_bounds__(kRasterThreads, 4) k_rasterN(CloudView c, ViewTable vt,
                                                            uint32_t view_base, Scratch s) {
     __shared__ uint32_t sh_atom[kMaxViewsPerLaunch];
     for (uint32_t i = threadIdx.x; i < kMaxViewsPerLaunch; i += blockDim.x) sh_atom[i] = 0;
@@ -1146,13 +1260,22 @@ __global__ void __launch_bounds__(kRasterThreads) k_rasterN(CloudView c, ViewTab
         }
         const pc_batch bt = c.batches[e.batch];
         const uint32_t p0 = bt.first + e.seg_first;
-        for (uint32_t mm = e.view_mask; mm; mm &= mm - 1) {
+        // certified views at k = 1 and at k = 2 share one decode each
+        uint32_t fast1 = 0, fast2 = 0;
+        for (uint32_t mm = e.view_mask & e.fast_mask; mm; mm &= mm - 1) {
+            const uint32_t v = __ffs(mm) - 1;
+            const uint32_t k = (uint32_t)((e.kcodes >> (2 * v)) & 3u);
+            if (k == 1) fast1 |= 1u << v;
+            if (k == 2) fast2 |= 1u << v;
+        }
+        if (fast1) segment_fast_views<1>(c, vt, fast1, bt, p0, p0 + e.seg_count, lane, sh_atom);
+        if (fast2) segment_fast_views<2>(c, vt, fast2, bt, p0, p0 + e.seg_count, lane, sh_atom);
+        for (uint32_t mm = e.view_mask & ~(fast1 | fast2); mm; mm &= mm - 1) {
             const uint32_t v = __ffs(mm) - 1;
             const ViewConst vc = make_view_const(vt.v[v]);
             const FastView fv = make_fast_view(vt.v[v]);
             const uint32_t n = segment_k<false>(c, vc, fv, bt, (int)((e.kcodes >> (2 * v)) & 3u),
-                                                (e.fast_mask >> v) & 1u, p0, p0 + e.seg_count,
-                                                lane, s);
+                                                false, p0, p0 + e.seg_count, lane);
             const uint32_t t = __reduce_add_sync(FULL, n);
             if (lane == 0 && t) atomicAdd(&sh_atom[v], t);
         }
@@ -1260,9 +1383,12 @@ __device__ __forceinline__ void shade_flush(ShadeRun& run, const ShadeBuf& sb, P
 // (nearly every point of a dense view falls within its pixel's window). The
 // loads go through L1, which keeps the other half of each 32-byte sector for
 // the lane's next group.
-template <int K, ShadeMode MODE>
+// FAST: a certified batch (batch_fast) at k <= 2, projected as in the depth
+// pass's fast path; every point is then in front of the eye and inside the view.
+template <int K, ShadeMode MODE, bool FAST>
 __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const ViewConst& vc,
-                                                  const ShadeBuf& sb, const DecConst& d,
+                                                  const FastView& fv, const ShadeBuf& sb,
+                                                  const DecConst& d, const FastDec& df,
                                                   uint32_t p0, uint32_t p1, uint32_t lane) {
     const uint32_t base = p0 & ~3u;
     const uint32_t groups = (p1 - base + 3u) >> 2;
@@ -1286,36 +1412,65 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
         if (K >= 2) q2w = ld_words<false>(c.w2 + g);
         if (K >= 3) q3w = ld_words<false>(c.w3 + g);
         const uint4 col = ld_words<false>(c.color + g);
-        float x[4], y[4], z[4];
-        decode_point<K>(d, q1w.x, q2w.x, q3w.x, x[0], y[0], z[0]);
-        decode_point<K>(d, q1w.y, q2w.y, q3w.y, x[1], y[1], z[1]);
-        decode_point<K>(d, q1w.z, q2w.z, q3w.z, x[2], y[2], z[2]);
-        decode_point<K>(d, q1w.w, q2w.w, q3w.w, x[3], y[3], z[3]);
         uint32_t pix[4], w[4], bx[4], by[4];
-        float cx[4], cy[4], cw[4];
         bool live[4];
-        uint32_t slow = 0;   // live points whose bracket did not settle the pixel
+        if (FAST) {
+            const uint32_t wa[4] = {q1w.x, q1w.y, q1w.z, q1w.w};
+            const uint32_t wb[4] = {q2w.x, q2w.y, q2w.z, q2w.w};
+            f2_t cxy[4];
+            float cw[4];
+            bool slow = false;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            clip_xyw(vc, x[j], y[j], z[j], cx[j], cy[j], cw[j]);
-            live[j] = cw[j] > 0.0f && g + j >= p0 && g + j < p1;
-            const bool ok = pixel_bits_fast(cx[j], cy[j], cw[j], vc.W, vc.H, bx[j], by[j]);
-            slow |= (uint32_t)(live[j] && !ok) << j;
-        }
-        if (slow) {
+            for (int j = 0; j < 4; ++j) {
+                fast_clip<K>(fv, df, wa[j], wb[j], cxy[j], cw[j]);
+                slow |= !pixel_bracket(fv, cxy[j], cw[j], bx[j], by[j]);
+            }
+            if (slow) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if ((slow >> j) & 1u) {
-                    bx[j] = exact_floor_bits(cx[j], cw[j], vc.W);
-                    by[j] = exact_floor_bits(cy[j], cw[j], vc.H);
+                for (int j = 0; j < 4; ++j) {
+                    float cx, cy;
+                    f2_unpack(cxy[j], cx, cy);
+                    bx[j] = exact_floor_bits(cx, cw[j], vc.W);
+                    by[j] = exact_floor_bits(cy, cw[j], vc.H);
                 }
-        }
+            }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t px = bx[j] - 0x4B000000u, py = by[j] - 0x4B000000u;
-            live[j] = live[j] && px < vc.width && py < vc.height;
-            w[j] = __float_as_uint(cw[j]);
-            pix[j] = py * vc.width + px;
+            for (int j = 0; j < 4; ++j) {
+                // inside the view by the certificate; the index is checked all the same
+                pix[j] = (by[j] - 0x4B000000u) * vc.width + (bx[j] - 0x4B000000u);
+                live[j] = g + j >= p0 && g + j < p1 && pix[j] < fv.npix;
+                w[j] = __float_as_uint(cw[j]);
+            }
+        } else {
+            float x[4], y[4], z[4];
+            decode_point<K>(d, q1w.x, q2w.x, q3w.x, x[0], y[0], z[0]);
+            decode_point<K>(d, q1w.y, q2w.y, q3w.y, x[1], y[1], z[1]);
+            decode_point<K>(d, q1w.z, q2w.z, q3w.z, x[2], y[2], z[2]);
+            decode_point<K>(d, q1w.w, q2w.w, q3w.w, x[3], y[3], z[3]);
+            float cx[4], cy[4], cw[4];
+            uint32_t slow = 0;   // live points whose bracket did not settle the pixel
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                clip_xyw(vc, x[j], y[j], z[j], cx[j], cy[j], cw[j]);
+                live[j] = cw[j] > 0.0f && g + j >= p0 && g + j < p1;
+                const bool ok = pixel_bits_fast(cx[j], cy[j], cw[j], vc.W, vc.H, bx[j], by[j]);
+                slow |= (uint32_t)(live[j] && !ok) << j;
+            }
+            if (slow) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if ((slow >> j) & 1u) {
+                        bx[j] = exact_floor_bits(cx[j], cw[j], vc.W);
+                        by[j] = exact_floor_bits(cy[j], cw[j], vc.H);
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t px = bx[j] - 0x4B000000u, py = by[j] - 0x4B000000u;
+                live[j] = live[j] && px < vc.width && py < vc.height;
+                w[j] = __float_as_uint(cw[j]);
+                pix[j] = py * vc.width + px;
+            }
         }
         // reads for the points that start a run, issued together
         uint32_t wmin[4];
@@ -1357,12 +1512,18 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
 
 template <ShadeMode MODE>
 __device__ __forceinline__ uint32_t shade_segment_k(const CloudView& c, const ViewConst& vc,
-                                                    const ShadeBuf& sb, const pc_batch& bt, int k,
+                                                    const FastView& fv, const ShadeBuf& sb,
+                                                    const pc_batch& bt, int k, bool fast,
                                                     uint32_t p0, uint32_t p1, uint32_t lane) {
     const DecConst d = make_dec_const(bt, k);
-    if (k == 1) return shade_segment<1, MODE>(c, vc, sb, d, p0, p1, lane);
-    if (k == 2) return shade_segment<2, MODE>(c, vc, sb, d, p0, p1, lane);
-    return shade_segment<3, MODE>(c, vc, sb, d, p0, p1, lane);
+    if (fast && k == 1)
+        return shade_segment<1, MODE, true>(c, vc, fv, sb, d, make_fast_dec<1>(bt), p0, p1, lane);
+    if (fast && k == 2)
+        return shade_segment<2, MODE, true>(c, vc, fv, sb, d, make_fast_dec<2>(bt), p0, p1, lane);
+    const FastDec none{};
+    if (k == 1) return shade_segment<1, MODE, false>(c, vc, fv, sb, d, none, p0, p1, lane);
+    if (k == 2) return shade_segment<2, MODE, false>(c, vc, fv, sb, d, none, p0, p1, lane);
+    return shade_segment<3, MODE, false>(c, vc, fv, sb, d, none, p0, p1, lane);
 }
 
 // Persistent warps take draw-list segments (a counter of their own); each
@@ -1371,10 +1532,10 @@ __device__ __forceinline__ uint32_t shade_segment_k(const CloudView& c, const Vi
 // 3 both), so that a launch of one layout carries only its own code; 0 is the
 // second pass for packed views, which returns at once unless one of its views
 // flagged a pixel.
-// (No __launch_bounds__: with it ptxas held this kernel to 32 registers and
-// spilled.)
+// Four blocks of 256 threads per SM (64 registers): the kernel waits on loads
+// and on the visibility reads at run starts, and more warps hide more of it.
 template <int LAYOUTS>
-__global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s,
+__global__ void __launch_bounds__(256, 4) k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s,
                         uint32_t shade_mask) {
     constexpr bool FALLBACK = LAYOUTS == 0;
     __shared__ uint32_t sh_blend[kMaxViewsPerLaunch];
@@ -1407,7 +1568,9 @@ __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s
         for (uint32_t mm = e.view_mask & shade_mask; mm; mm &= mm - 1) {
             const uint32_t v = __ffs(mm) - 1;
             const ViewConst vc = make_view_const(vt.v[v]);
+            const FastView fv = make_fast_view(vt.v[v]);
             const int k = (int)((e.kcodes >> (2 * v)) & 3u);
+            const bool fast = (e.fast_mask >> v) & 1u;
             const ViewParams& vp = vt.v[v];
             const uint64_t npix = (uint64_t)vp.width * vp.height;
             ShadeBuf sb;
@@ -1417,14 +1580,14 @@ __global__ void k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s
             sb.fallback_pixels = &s.stats[(uint64_t)(view_base + v) * S_COUNT + S_FALLBACK];
             uint32_t n;
             if (FALLBACK)
-                n = shade_segment_k<ShadeMode::kFallback>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
-                                                          lane);
+                n = shade_segment_k<ShadeMode::kFallback>(c, vc, fv, sb, bt, k, fast, p0,
+                                                          p0 + e.seg_count, lane);
             else if (LAYOUTS == 2 || (LAYOUTS == 3 && (vp.flags & PC_VIEW_HQS_PACKED)))
-                n = shade_segment_k<ShadeMode::kPacked>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
-                                                        lane);
+                n = shade_segment_k<ShadeMode::kPacked>(c, vc, fv, sb, bt, k, fast, p0,
+                                                        p0 + e.seg_count, lane);
             else
-                n = shade_segment_k<ShadeMode::kTwoWord>(c, vc, sb, bt, k, p0, p0 + e.seg_count,
-                                                         lane);
+                n = shade_segment_k<ShadeMode::kTwoWord>(c, vc, fv, sb, bt, k, fast, p0,
+                                                         p0 + e.seg_count, lane);
             const uint32_t t = __reduce_add_sync(FULL, n);
             if (lane == 0 && t) atomicAdd(&sh_blend[v], t);
         }

@@ -119,10 +119,17 @@ def test_poll_wait_is_bounded(world):
     """pc_poll has no unbounded wait: a negative timeout is refused, and a
     request still queued behind others answers PC_ETIMEDOUT after about the
     timeout it was given."""
+    import torch
     ctx, (c1, p1), _ = world
-    views = [pcr.make_view(S.random_view(p1, 80 + i, 2048, 2048, seed=4), 2048, 2048,
+    W = H = 1024
+    views = [pcr.make_view(S.random_view(p1, 80 + i, W, H, seed=4), W, H,
                            pcr.PC_VIEW_CULL | pcr.PC_VIEW_NO_EARLY_DEPTH) for i in range(8)]
-    tickets = [pcr.pc_submit(ctx.h, c1, views) for _ in range(8)]
+    # caller-owned framebuffers: a long queue without pool admission or host images
+    fbs = [[(torch.empty(W * H, dtype=torch.int64, device="cuda"),
+             torch.empty(W * H, dtype=torch.int32, device="cuda")) for _ in views]
+           for _ in range(12)]
+    tickets = [pcr.pc_submit(ctx.h, c1, views, [(a.data_ptr(), b.data_ptr()) for a, b in fb])
+               for fb in fbs]
     with pytest.raises(pcr.PCError) as e:
         pcr.pc_poll(ctx.h, tickets[-1], -1)
     assert e.value.status == pcr.PC_EINVAL
