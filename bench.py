@@ -355,6 +355,37 @@ def serving_bench(args, pcr, ctx, clouds):
                        "views_per_s_one_view_per_launch": s1["views_per_s"],
                        "speedup": b["views_per_s"] / s1["views_per_s"],
                        "p50_ms_batched": b["p50_ms"], "p50_ms_one_view_per_launch": s1["p50_ms"]}
+    # the smallest cloud, 96 requests of one 1280x720 view each into caller-owned
+    # device framebuffers (images stay on the GPU: no pool admission, no copy to
+    # the host), every request submitted at once
+    import torch
+    cloud_s, params_s, name_s = clouds[-1]
+    dviews = [[pcr.make_view(pcsynth.random_view(params_s, 3000 + i, 1280, 720, seed=args.seed),
+                             1280, 720, pcr.PC_VIEW_CULL)] for i in range(96)]
+    dfbs = [(torch.empty(1280 * 720, dtype=torch.int64, device="cuda"),
+             torch.empty(1280 * 720, dtype=torch.int32, device="cuda")) for _ in dviews]
+
+    def run_dev(vpl):
+        pcr.pc_set_views_per_launch(ctx.h, vpl)
+        tks = [pcr.pc_submit(ctx.h, cloud_s, v, [(a.data_ptr(), b.data_ptr())])
+               for v, (a, b) in zip(dviews, dfbs)]
+        t_sub, t_done = [], []
+        for tk in tks:
+            rc, res = pcr.pc_poll(ctx.h, tk, 60000, copy_images=False)
+            if rc != pcr.PC_OK or res["status"] != pcr.PC_OK:
+                raise RuntimeError("device-framebuffer request failed")
+            t_sub.append(res["t_submit_ms"])
+            t_done.append(res["t_done_ms"])
+            pcr.pc_release_ticket(ctx.h, tk)
+        lat = np.array(t_done) - np.array(t_sub)
+        return {"views_per_s": len(dviews) / ((max(t_done) - min(t_sub)) / 1e3),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    run_dev(0)   # warm-up
+    dev_b, dev_s = run_dev(0), run_dev(1)
+    device_fb = {"cloud": name_s, "requests": len(dviews), "resolution": "1280x720",
+                 "batched": dev_b, "one_view_per_launch": dev_s,
+                 "speedup": dev_b["views_per_s"] / dev_s["views_per_s"]}
     pcr.pc_set_views_per_launch(ctx.h, 0)
     return {"requests": len(reqs), "views": nviews,
             "clouds": [c[2] for c in clouds],
@@ -365,7 +396,7 @@ def serving_bench(args, pcr, ctx, clouds):
             "p99_ms": batched["p99_ms"], "saturated": batched,
             "one_view_per_launch": single,
             "speedup_vs_one_view_per_launch": batched["views_per_s"] / single["views_per_s"],
-            "sustainable": loads, "each_cloud_alone": alone,
+            "sustainable": loads, "each_cloud_alone": alone, "device_framebuffers": device_fb,
             "identical_bits": same, "identical_bits_checked": "every image of every request, "
             "batched vs one view per launch, in untimed runs",
             "all_ok": batched["ok"] and single["ok"]}

@@ -884,6 +884,7 @@ struct FastView {
     f2_t wh;                     // (W, H)
     uint32_t width;
     uint32_t npix;               // width * height
+    uint32_t pixbias;            // -(2^23 bits) (width + 1): pixel = by width + bx + pixbias
     unsigned long long* vis;
 };
 
@@ -903,6 +904,7 @@ __device__ __forceinline__ FastView make_fast_view(const ViewParams& v) {
     f.wh = f2_pack((float)v.width, (float)v.height);
     f.width = v.width;
     f.npix = v.width * v.height;
+    f.pixbias = 0u - 0x4B000000u * (v.width + 1u);
     f.vis = reinterpret_cast<unsigned long long*>(v.vis);
     return f;
 }
@@ -1018,7 +1020,7 @@ __device__ __forceinline__ uint32_t raster_decoded(const FastView& fv, const f2_
     for (int j = 0; j < 4; ++j) {
         // the certificate puts every pixel inside the view, so the clamp changes
         // nothing; it only keeps every access inside the buffer
-        pix[j] = min((by[j] - 0x4B000000u) * fv.width + (bx[j] - 0x4B000000u), fv.npix - 1u);
+        pix[j] = min(by[j] * fv.width + bx[j] + fv.pixbias, fv.npix - 1u);
         w[j] = __float_as_uint(cw[j]);
         lim[j] = vis_hi[2ull * pix[j]];
     }
