@@ -1090,19 +1090,31 @@ __device__ __forceinline__ uint32_t segment_fast(const CloudView& c, const ViewC
         base += 128u;
     }
     if (base + 128u <= p1) {
+        // whole steps: the next step's words are loaded while the current one
+        // is projected; the last step is peeled so that the loop carries no
+        // bounds test, and two steps are unrolled
         const FastDec d = make_fast_dec<K>(bt);
-        uint4 n1 = ld_words<STREAM>(c.w1 + base + 4u * lane);
+        const uint32_t nsteps = (p1 - base) >> 7;
+        uint32_t g = base + 4u * lane;
+        const uint32_t* a1 = c.w1 + g;
+        const uint32_t* a2 = K >= 2 ? c.w2 + g : nullptr;
+        uint4 n1 = ld_words<STREAM>(a1);
         uint4 n2 = make_uint4(0, 0, 0, 0);
-        if (K >= 2) n2 = ld_words<STREAM>(c.w2 + base + 4u * lane);
-        for (; base + 128u <= p1; base += 128u) {
-            const uint32_t g = base + 4u * lane;
+        if (K >= 2) n2 = ld_words<STREAM>(a2);
+#pragma unroll 2
+        for (uint32_t st = 1; st < nsteps; ++st) {
             const uint4 q1 = n1, q2 = n2;
-            if (base + 256u <= p1) {
-                n1 = ld_words<STREAM>(c.w1 + g + 128u);
-                if (K >= 2) n2 = ld_words<STREAM>(c.w2 + g + 128u);
+            a1 += 128;
+            n1 = ld_words<STREAM>(a1);
+            if (K >= 2) {
+                a2 += 128;
+                n2 = ld_words<STREAM>(a2);
             }
             n_atom += raster_group_fast<K>(fv, d, q1, q2, g);
+            g += 128u;
         }
+        n_atom += raster_group_fast<K>(fv, d, n1, n2, g);
+        base += nsteps << 7;
     }
     if (base < p1) {
         const uint32_t g = base + 4u * lane;
