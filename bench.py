@@ -44,7 +44,7 @@ METRIC = "Gpoints/s & ms/frame at 2B pts 1080p; %HBM peak; batched views/s, p50/
 # launch is this scaled by the points processed. Re-capture when the kernel changes.
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
 RASTER_CAPTURE_POINTS = 50_000_000
-RASTER_CAPTURE_DRAM_BYTES = 210_563_328
+RASTER_CAPTURE_DRAM_BYTES = 210_849_024
 
 
 def parse():
