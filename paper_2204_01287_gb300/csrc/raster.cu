@@ -1374,6 +1374,23 @@ __device__ __forceinline__ void hqs_add(const ShadeBuf& sb, PendingAdd& pend, ui
     }
 }
 
+// Predicated 32-bit load: 0 when p is false, and then no access is made.
+__device__ __forceinline__ uint32_t ld_u32_if(bool p, const uint32_t* a) {
+    uint32_t v = 0;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.u32 %0, [%1];\n\t}"
+        : "+r"(v)
+        : "l"(a), "r"((uint32_t)p));
+    return v;
+}
+
+// Predicated 64-bit reduction: no access when p is false.
+__device__ __forceinline__ void red_add_if(bool p, unsigned long long* a, unsigned long long v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.global.add.u64 [%0], %1;\n\t}"
+                 :
+                 : "l"(a), "l"(v), "r"((uint32_t)p)
+                 : "memory");
+}
+
 // Running sums of one lane: the pixel of its current run of points, that
 // pixel's depth limit fl(w_min * 1.01f) and (second pass) its fallback flag.
 struct ShadeRun {
@@ -1485,6 +1502,44 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
                 w[j] = __float_as_uint(cw[j]);
                 pix[j] = py * vc.width + px;
             }
+        }
+        if (MODE == ShadeMode::kTwoWord) {
+            // Straight-line form of the run walk below, without branches: a
+            // point that starts a run flushes the lane's sums (two predicated
+            // reductions, skipped when the run blended nothing) and takes its
+            // pixel's limit; every point adds its colour when it passes.
+            const uint32_t cc[4] = {col.x, col.y, col.z, col.w};
+            bool st[4];
+            uint32_t wm[4];
+            uint32_t prev = run.pix;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                st[j] = live[j] && pix[j] != prev;
+                prev = live[j] ? pix[j] : prev;
+                wm[j] = ld_u32_if(st[j], vis_hi + 2ull * pix[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool f = st[j] && run.n != 0u;
+                unsigned long long* a = sb.sums + 2ull * run.pix;
+                red_add_if(f, a, (unsigned long long)run.r | ((unsigned long long)run.g << 32));
+                red_add_if(f, a + 1, (unsigned long long)run.b | ((unsigned long long)run.n << 32));
+                run.pix = st[j] ? pix[j] : run.pix;
+                run.limit = st[j] ? __fmul_rn(__uint_as_float(wm[j]), 1.01f) : run.limit;
+                run.r = st[j] ? 0u : run.r;
+                run.g = st[j] ? 0u : run.g;
+                run.b = st[j] ? 0u : run.b;
+                run.n = st[j] ? 0u : run.n;
+                const bool t = live[j] && __uint_as_float(w[j]) <= run.limit;
+                if (t) {
+                    run.r += cc[j] & 255u;
+                    run.g += __byte_perm(cc[j], 0u, 0x4441);
+                    run.b += __byte_perm(cc[j], 0u, 0x4442);
+                    run.n += 1;
+                    ++n_blend;
+                }
+            }
+            continue;
         }
         // reads for the points that start a run, issued together
         uint32_t wmin[4];

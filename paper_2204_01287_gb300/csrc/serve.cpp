@@ -7,10 +7,13 @@
 // max_views_per_launch views), and runs up to serve_streams groups at once on
 // their own CUDA streams. Requests that arrive while groups are on the GPU join
 // the next group that starts, so work of several requests overlaps on the
-// device. Each group copies its images to pinned host memory and signals the
-// scheduler from a host callback on its stream; pc_poll waits on a condition
-// variable with a bounded timeout. Every wait in this file is bounded or woken
-// by a state change; nothing waits on the device without a limit.
+// device. Each group copies its images to pinned host memory on a second
+// stream of its lane, which waits for the group's render only: the lane takes
+// its next group as soon as the render is done, so the next render overlaps
+// the image copies. Host callbacks signal the end of a render and of a group's
+// copies; pc_poll waits on a condition variable with a bounded timeout. Every
+// wait in this file is bounded or woken by a state change; nothing waits on the
+// device without a limit.
 #include <algorithm>
 #include <cstring>
 #include <deque>
@@ -45,10 +48,13 @@ struct Request {
 };
 
 struct Lane {
-    cudaStream_t stream = nullptr;
-    std::vector<Request*> reqs;
-    bool busy = false;
-    bool finished = false;            // set by the host callback
+    cudaStream_t stream = nullptr;        // renders
+    cudaStream_t copy_stream = nullptr;   // image copies and completion
+    cudaEvent_t rendered = nullptr;       // end of the latest render
+    bool busy = false;                    // a render is in flight
+    bool finished = false;                // its end was signalled (host callback)
+    std::deque<std::vector<Request*>> groups;   // groups not yet complete, oldest first
+    uint32_t completed = 0;               // completion callbacks not yet retired
 };
 
 }  // namespace serve_detail
@@ -73,15 +79,24 @@ struct ServeState {
 
 namespace {
 
-void CUDART_CB lane_done(void* p) {
+struct LaneSignal {
+    ServeState* s;
+    Lane* lane;
+    bool copies;   // false: end of a render, true: end of a group's copies
+};
+
+void CUDART_CB lane_signal(void* p) {
     // runs on a CUDA callback thread: no CUDA calls here
-    auto* pair = static_cast<std::pair<ServeState*, Lane*>*>(p);
+    auto* sig = static_cast<LaneSignal*>(p);
     {
-        std::lock_guard<std::mutex> g(pair->first->mu);
-        pair->second->finished = true;
+        std::lock_guard<std::mutex> g(sig->s->mu);
+        if (sig->copies)
+            ++sig->lane->completed;
+        else
+            sig->lane->finished = true;
     }
-    pair->first->cv_work.notify_all();
-    delete pair;
+    sig->s->cv_work.notify_all();
+    delete sig;
 }
 
 void release_device(ServeState& s, Request& r) {
@@ -116,38 +131,59 @@ void launch_group(ServeState& s, Lane& lane, std::vector<Request*>& group) {
     Slot* slot = ctx.slot_for(lane.stream);
     pc_status rc = ctx.render(*group[0]->cloud, views.data(), (uint32_t)views.size(), fbs.data(),
                               lane.stream, slot);
+    // the copies wait for this render only, on the lane's copy stream
+    cudaError_t e = cudaEventRecord(lane.rendered, lane.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(lane.copy_stream, lane.rendered, 0);
+    if (e != cudaSuccess && rc == PC_OK) rc = ctx.cuda_fail(e, "serving stream order");
     size_t k = 0;
     for (Request* r : group) {
         for (size_t v = 0; v < r->views.size(); ++v, ++k) {
             if (rc != PC_OK) break;
             if (!r->user_fb.empty()) continue;   // the images stay in the caller's framebuffers
             const uint64_t npix = (uint64_t)r->views[v].width * r->views[v].height;
-            cudaError_t e = cudaMemcpyAsync(r->host[v], fbs[k].rgba, npix * 4,
-                                            cudaMemcpyDeviceToHost, lane.stream);
+            e = cudaMemcpyAsync(r->host[v], fbs[k].rgba, npix * 4, cudaMemcpyDeviceToHost,
+                                lane.copy_stream);
             if (e != cudaSuccess) rc = ctx.cuda_fail(e, "serving image copy");
         }
         if (rc != PC_OK) r->status = rc;
     }
-    auto* pair = new std::pair<ServeState*, Lane*>(&s, &lane);
-    if (cudaLaunchHostFunc(lane.stream, lane_done, pair) != cudaSuccess) {
-        delete pair;
+    auto* rendered = new LaneSignal{&s, &lane, false};
+    auto* copied = new LaneSignal{&s, &lane, true};
+    const bool ok_render = cudaLaunchHostFunc(lane.stream, lane_signal, rendered) == cudaSuccess;
+    const bool ok_copies = cudaLaunchHostFunc(lane.copy_stream, lane_signal, copied) == cudaSuccess;
+    if (!ok_render) delete rendered;
+    if (!ok_copies) delete copied;
+    if (!ok_render || !ok_copies) {
+        // a callback that cannot be queued is signalled here: the lane is
+        // retired on the next pass and the statuses show the failure (a queued
+        // callback of the other kind still arrives and finds nothing to do)
         std::lock_guard<std::mutex> g(s.mu);
-        lane.finished = true;   // retire on the next pass; status shows the failure
+        if (!ok_render) lane.finished = true;
+        if (!ok_copies) ++lane.completed;
         for (Request* r : group)
             if (r->status == PC_OK) r->status = PC_ECUDA;
     }
 }
 
+// Retire the lane's completed groups (oldest first) and free its render slot
+// once its render has ended (called with s.mu held).
 void retire(ServeState& s, Lane& lane) {
-    const double t = s.ctx->now_ms();
-    for (Request* r : lane.reqs) {
-        release_device(s, *r);
-        r->t_done = t;
-        r->state = R_DONE;
+    if (lane.busy && lane.finished) {
+        lane.busy = false;
+        lane.finished = false;
     }
-    lane.reqs.clear();
-    lane.busy = false;
-    lane.finished = false;
+    if (!lane.completed) return;
+    const double t = s.ctx->now_ms();
+    while (lane.completed && !lane.groups.empty()) {
+        for (Request* r : lane.groups.front()) {
+            release_device(s, *r);
+            r->t_done = t;
+            r->state = R_DONE;
+        }
+        lane.groups.pop_front();
+        --lane.completed;
+    }
+    lane.completed = 0;
     s.cv_done.notify_all();
 }
 
@@ -199,8 +235,7 @@ void scheduler(ServeState* sp) {
     cudaSetDevice(s.ctx->device);
     std::unique_lock<std::mutex> lk(s.mu);
     while (!s.stop) {
-        for (auto& l : s.lanes)
-            if (l->busy && l->finished) retire(s, *l);
+        for (auto& l : s.lanes) retire(s, *l);
         bool launched = false;
         for (auto& l : s.lanes) {
             if (l->busy) continue;
@@ -211,7 +246,7 @@ void scheduler(ServeState* sp) {
                 r->t_start = t;
                 r->state = R_RUNNING;
             }
-            l->reqs = group;
+            l->groups.push_back(group);
             l->busy = true;
             l->finished = false;
             lk.unlock();
@@ -238,10 +273,12 @@ void serve_shutdown(Ctx& ctx) {
     s->cv_work.notify_all();
     if (s->th.joinable()) s->th.join();
     for (auto& l : s->lanes) {
-        if (l->stream) {
-            cudaStreamSynchronize(l->stream);
-            cudaStreamDestroy(l->stream);
+        for (cudaStream_t st : {l->stream, l->copy_stream}) {
+            if (!st) continue;
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
         }
+        if (l->rendered) cudaEventDestroy(l->rendered);
     }
     cudaFree(s->dev_base);
     cudaFreeHost(s->host_base);
@@ -266,10 +303,24 @@ static pc_status serve_start(Ctx& ctx) {
     }
     s->dev.init(dev_bytes);
     s->host.init(host_bytes);
-    for (uint32_t i = 0; i < ctx.cfg.serve_streams; ++i) {
+    for (uint32_t i = 0; i < ctx.cfg.serve_streams && e == cudaSuccess; ++i) {
         auto l = std::make_unique<Lane>();
-        cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking);
+        e = cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l->rendered, cudaEventDisableTiming);
         s->lanes.push_back(std::move(l));
+    }
+    if (e != cudaSuccess) {
+        for (auto& l : s->lanes) {
+            if (l->stream) cudaStreamDestroy(l->stream);
+            if (l->copy_stream) cudaStreamDestroy(l->copy_stream);
+            if (l->rendered) cudaEventDestroy(l->rendered);
+        }
+        cudaFree(s->dev_base);
+        cudaFreeHost(s->host_base);
+        delete s;
+        ctx.fail_msg("serving streams: %s", cudaGetErrorString(e));
+        return PC_ECUDA;
     }
     ctx.serve = s;
     s->th = std::thread(scheduler, s);
