@@ -1465,11 +1465,13 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
                     by[j] = exact_floor_bits(cy, cw[j], vc.H);
                 }
             }
+            // points g + lo .. g + hi - 1 of the group lie in [p0, p1)
+            const uint32_t lo = p0 > g ? p0 - g : 0u, hi = p1 - g;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                // inside the view by the certificate; the index is checked all the same
-                pix[j] = (by[j] - 0x4B000000u) * vc.width + (bx[j] - 0x4B000000u);
-                live[j] = g + j >= p0 && g + j < p1 && pix[j] < fv.npix;
+                // inside the view by the certificate; the index is clamped all the same
+                pix[j] = min(by[j] * fv.width + bx[j] + fv.pixbias, fv.npix - 1u);
+                live[j] = (uint32_t)j >= lo && (uint32_t)j < hi;
                 w[j] = __float_as_uint(cw[j]);
             }
         } else {
