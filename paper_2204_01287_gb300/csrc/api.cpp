@@ -178,7 +178,7 @@ RasterShape Ctx::shape_for(const Cloud& cl, uint32_t nviews) {
                           : t.threads_per_block ? t.threads_per_block : 256;
     int per_sm = cfg.blocks_per_sm ? (int)cfg.blocks_per_sm
                  : t.blocks_per_sm ? t.blocks_per_sm
-                                   : raster_occupancy(r.threads_per_block, nviews > 1);
+                                   : raster_occupancy(r.threads_per_block, nviews);
     r.blocks = num_sms * per_sm;
     return r;
 }

@@ -97,7 +97,7 @@ extern "C" pc_status pc_autotune(pc_ctx* h, pc_cloud cloud, const pc_view* views
     pc_status rc = PC_OK;
     cl->tuned_vpl = 1;
     for (int tpb : {128, 256}) {
-        const int occ = raster_occupancy(tpb, false);
+        const int occ = raster_occupancy(tpb, 1);
         for (int bps = std::max(1, occ / 2); bps <= occ && rc == PC_OK; ++bps) {
             for (uint32_t seg : {1024u, 2048u, 4096u}) {
                 Tune t;

@@ -174,8 +174,9 @@ cudaError_t launch_merge_min(uint64_t* dst, const uint64_t* src, uint64_t n, cud
 PCR_HD inline unsigned long long empty_key(uint32_t flags) {
     return (flags & PC_VIEW_SIGNED_EMPTY) ? 0x7FFFFFFFFFFFFFFFull : ~0ull;
 }
-// Blocks per SM the raster kernel can keep resident at a block size.
-int raster_occupancy(int threads_per_block, bool multiview);
+// Blocks per SM the raster kernel of a launch of nviews views can keep
+// resident at a block size.
+int raster_occupancy(int threads_per_block, uint32_t nviews);
 
 // ---- host encoder (encoder.cpp) -------------------------------------------
 

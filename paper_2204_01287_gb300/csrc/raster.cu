@@ -1196,6 +1196,82 @@ __device__ __forceinline__ void segment_fast_views(const CloudView& c, const Vie
     }
 }
 
+// Points [p0, p1) of a certified batch at precision K for views 0 and 1 of a
+// two-view launch (vmask: bit v set when view v is certified at K): one decode
+// per step as in segment_fast_views, then each view with its constants read at
+// fixed parameter offsets, as in the one-view kernel (a view index that is
+// only known at run time makes them loads).
+template <int K>
+__device__ __forceinline__ void segment_fast_pair(const CloudView& c, const ViewTable& vt,
+                                                  uint32_t vmask, const pc_batch& bt,
+                                                  uint32_t p0, uint32_t p1, uint32_t lane,
+                                                  uint32_t& na0, uint32_t& na1) {
+    uint32_t base = p0 & ~3u;
+    if (lane == 0 && p1 > base) {
+        const uint32_t bytes = ((p1 - base) * 4u + 15u) & ~15u;
+        prefetch_l2(c.w1 + base, bytes);
+        if (K >= 2) prefetch_l2(c.w2 + base, bytes);
+    }
+    // the ragged first and last steps view by view on the general path
+    auto partial = [&](uint32_t g, uint32_t valid) {
+        if (vmask & 1u)
+            na0 += raster_group<K, false, true>(c, make_view_const(vt.v[0]), make_dec_const(bt, K),
+                                                g, valid);
+        if (vmask & 2u)
+            na1 += raster_group<K, false, true>(c, make_view_const(vt.v[1]), make_dec_const(bt, K),
+                                                g, valid);
+    };
+    if (base != p0 && base < p1) {
+        const uint32_t g = base + 4u * lane;
+        if (g < p1) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j >= p0 && g + j < p1) << j;
+            partial(g, valid);
+        }
+        base += 128u;
+    }
+    if (base + 128u <= p1) {
+        const FastDec d = make_fast_dec<K>(bt);
+        const uint32_t nsteps = (p1 - base) >> 7;
+        uint32_t g = base + 4u * lane;
+        const uint32_t* a1 = c.w1 + g;
+        const uint32_t* a2 = K >= 2 ? c.w2 + g : nullptr;
+        uint4 n1 = ld_words<true>(a1);
+        uint4 n2 = make_uint4(0, 0, 0, 0);
+        if (K >= 2) n2 = ld_words<true>(a2);
+        auto step = [&](const uint4& q1, const uint4& q2) {
+            f2_t xy[4];
+            float z[4];
+            decode_group<K>(d, q1, q2, xy, z);
+            if (vmask & 1u) na0 += raster_decoded(make_fast_view(vt.v[0]), xy, z, g);
+            if (vmask & 2u) na1 += raster_decoded(make_fast_view(vt.v[1]), xy, z, g);
+        };
+        for (uint32_t st = 1; st < nsteps; ++st) {
+            const uint4 q1 = n1, q2 = n2;
+            a1 += 128;
+            n1 = ld_words<true>(a1);
+            if (K >= 2) {
+                a2 += 128;
+                n2 = ld_words<true>(a2);
+            }
+            step(q1, q2);
+            g += 128u;
+        }
+        step(n1, n2);
+        base += nsteps << 7;
+    }
+    if (base < p1) {
+        const uint32_t g = base + 4u * lane;
+        if (g < p1) {
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) valid |= (uint32_t)(g + j < p1) << j;
+            partial(g, valid);
+        }
+    }
+}
+
 constexpr int kRasterThreads = 256;
 
 __device__ __forceinline__ bool next_entry(const Scratch& s, uint32_t n_entries, uint32_t lane,
@@ -1252,6 +1328,45 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_raster1(CloudView c, View
                                   p0 + e.seg_count, lane);
     }
     flush_atomics(s, view_base, n_atom, lane);
+}
+
+// Two views per launch (a stereo pair, Sec. 3.7): as k_rasterN, with both
+// views' constants at fixed parameter offsets. Four blocks of 256 threads per
+// SM (64 registers).
+__global__ void __launch_bounds__(kRasterThreads, 4) k_raster2(CloudView c, ViewTable vt,
+                                                           uint32_t view_base, Scratch s) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n_entries = s.counters[C_ENTRIES];
+    uint32_t na0 = 0, na1 = 0;
+    DrawEntry e;
+    while (next_entry(s, n_entries, lane, e)) {
+        if (e.batch >= c.n_batches) {
+            if (lane == 0) raise_error(s, E_BATCH_RANGE, e.batch);
+            continue;
+        }
+        const pc_batch bt = c.batches[e.batch];
+        const uint32_t p0 = bt.first + e.seg_first, p1 = p0 + e.seg_count;
+        // certified views at k = 1 and at k = 2 share one decode each
+        uint32_t fast1 = 0, fast2 = 0;
+#pragma unroll
+        for (uint32_t v = 0; v < 2; ++v) {
+            if (!(((e.view_mask & e.fast_mask) >> v) & 1u)) continue;
+            const uint32_t k = (e.kcodes >> (2 * v)) & 3u;
+            if (k == 1) fast1 |= 1u << v;
+            if (k == 2) fast2 |= 1u << v;
+        }
+        if (fast1) segment_fast_pair<1>(c, vt, fast1, bt, p0, p1, lane, na0, na1);
+        if (fast2) segment_fast_pair<2>(c, vt, fast2, bt, p0, p1, lane, na0, na1);
+        const uint32_t rest = e.view_mask & ~(fast1 | fast2);
+        if (rest & 1u)
+            na0 += segment_k<false>(c, make_view_const(vt.v[0]), make_fast_view(vt.v[0]), bt,
+                                    (int)(e.kcodes & 3u), false, p0, p1, lane);
+        if (rest & 2u)
+            na1 += segment_k<false>(c, make_view_const(vt.v[1]), make_fast_view(vt.v[1]), bt,
+                                    (int)((e.kcodes >> 2) & 3u), false, p0, p1, lane);
+    }
+    flush_atomics(s, view_base, na0, lane);
+    flush_atomics(s, view_base + 1, na1, lane);
 }
 
 // Several views per launch (Sec. 3.7): the views certified for a segment's
@@ -1830,11 +1945,12 @@ cudaError_t launch_cull(const CloudView& c, const ViewTable& vt, uint32_t view_b
     return cudaGetLastError();
 }
 
-int raster_occupancy(int threads_per_block, bool multiview) {
+int raster_occupancy(int threads_per_block, uint32_t nviews) {
     int nb = 0;
-    cudaError_t e = multiview
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rasterN, threads_per_block, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_raster1, threads_per_block, 0);
+    cudaError_t e =
+        nviews > 2    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rasterN, threads_per_block, 0)
+        : nviews == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_raster2, threads_per_block, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_raster1, threads_per_block, 0);
     if (e != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
@@ -1843,9 +1959,9 @@ cudaError_t launch_raster(const CloudView& c, const ViewTable& vt, uint32_t view
                           RasterShape shape, cudaStream_t st) {
     int threads = shape.threads_per_block > 0 ? shape.threads_per_block : kRasterThreads;
     threads = threads > kRasterThreads ? kRasterThreads : (threads < 32 ? 32 : threads & ~31);
-    const bool multi = vt.n > 1;
-    int blocks = shape.blocks > 0 ? shape.blocks : num_sms() * raster_occupancy(threads, multi);
-    if (multi) k_rasterN<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
+    int blocks = shape.blocks > 0 ? shape.blocks : num_sms() * raster_occupancy(threads, vt.n);
+    if (vt.n > 2) k_rasterN<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
+    else if (vt.n == 2) k_raster2<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
     else k_raster1<<<blocks, threads, 0, st>>>(c, vt, view_base, s);
     return cudaGetLastError();
 }
