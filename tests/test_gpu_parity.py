@@ -157,6 +157,26 @@ def test_multiview_equals_single(ctx, terrain_small, nv):
         assert_same(multi[i][0], multi[i][1], ovis, enc.color, f"view {i}/{nv}")
 
 
+@pytest.mark.parametrize("ks", [(2, 2), (1, 2), (3, 1), (0, 3)])
+def test_two_views_mixed_precision(ctx, terrain_small, ks):
+    """Two-view launches (the stereo kernel): both views certified at one k
+    share a decode, at different k each takes its own, and a view at k = 3
+    or an uncertified one takes the general path; every image equals its
+    single-view image and the oracle's."""
+    p, enc, cloud = terrain_small
+    views = []
+    for i, k in enumerate(ks):
+        flags = pcr.PC_VIEW_CULL | (pcr.PC_VIEW_FORCE_K(k) if k else 0)
+        views.append(pcr.make_view(S.random_view(p, 300 + i, 150, 110, seed=4), 150, 110, flags))
+    pair = gpu_render(ctx, cloud, views)
+    for i, v in enumerate(views):
+        [(vis, img)] = gpu_render(ctx, cloud, [v])
+        assert np.array_equal(pair[i][0], vis)
+        assert np.array_equal(pair[i][1], img)
+        ovis, _ = O.render(enc, oracle_view(np.array(v.view_proj), v.width, v.height, force_k=ks[i]))
+        assert_same(pair[i][0], pair[i][1], ovis, enc.color, f"view {i} of {ks}")
+
+
 def test_stereo_pair_one_launch(ctx, terrain_small):
     p, enc, cloud = terrain_small
     W, H = 126, 140
