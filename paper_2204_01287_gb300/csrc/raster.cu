@@ -1506,6 +1506,13 @@ __device__ __forceinline__ void red_add_if(bool p, unsigned long long* a, unsign
                  : "memory");
 }
 
+// 32 bytes from a 32-byte aligned address on the read-only path: one sector.
+__device__ __forceinline__ void ld_words8(const uint32_t* p, uint4& a, uint4& b) {
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
+
 // Running sums of one lane: the pixel of its current run of points, that
 // pixel's depth limit fl(w_min * 1.01f) and (second pass) its fallback flag.
 struct ShadeRun {
@@ -1522,13 +1529,14 @@ __device__ __forceinline__ void shade_flush(ShadeRun& run, const ShadeBuf& sb, P
 }
 
 // Points [p0, p1) of one batch for one shaded view at precision K. Each lane
-// walks its own contiguous share of the segment, 4 points at a time, so that
-// consecutive points (Morton order makes them neighbours) extend one run: the
-// visibility buffer is read only where a run starts, and one addition per run
-// reaches the sums. The colour words are loaded with the coordinate words
-// (nearly every point of a dense view falls within its pixel's window). The
-// loads go through L1, which keeps the other half of each 32-byte sector for
-// the lane's next group.
+// walks its own contiguous share of the segment, so that consecutive points
+// (Morton order makes them neighbours) extend one run: the visibility buffer is
+// read only where a run starts, and one addition per run reaches the sums. The
+// colour words are loaded with the coordinate words (nearly every point of a
+// dense view falls within its pixel's window). At k <= 2 a lane takes 8 points
+// per step with 32-byte loads, each of which fills one sector (the cloud's
+// arrays are 32-byte aligned and padded past the last 8-point step); otherwise
+// 4 points per step with 16-byte loads.
 // FAST: a certified batch (batch_fast) at k <= 2, projected as in the depth
 // pass's fast path; every point is then in front of the eye and inside the view.
 template <int K, ShadeMode MODE, bool FAST>
@@ -1551,13 +1559,8 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
     pend.n = 0;
     pend.pix = 0;
     uint32_t n_blend = 0;
-    for (uint32_t q = q0; q < q1; ++q) {
-        const uint32_t g = base + 4u * q;
-        const uint4 q1w = ld_words<false>(c.w1 + g);
-        uint4 q2w = make_uint4(0, 0, 0, 0), q3w = make_uint4(0, 0, 0, 0);
-        if (K >= 2) q2w = ld_words<false>(c.w2 + g);
-        if (K >= 3) q3w = ld_words<false>(c.w3 + g);
-        const uint4 col = ld_words<false>(c.color + g);
+    auto group = [&](uint32_t g, const uint4& q1w, const uint4& q2w, const uint4& q3w,
+                     const uint4& col) {
         uint32_t pix[4], w[4], bx[4], by[4];
         bool live[4];
         if (FAST) {
@@ -1656,7 +1659,7 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
                     ++n_blend;
                 }
             }
-            continue;
+            return;
         }
         // reads for the points that start a run, issued together
         uint32_t wmin[4];
@@ -1689,6 +1692,34 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
                 run.n += 1;
                 ++n_blend;
             }
+        }
+    };
+    if (K <= 2 && ((reinterpret_cast<uintptr_t>(c.w1) | reinterpret_cast<uintptr_t>(c.color) |
+                    (K >= 2 ? reinterpret_cast<uintptr_t>(c.w2) : 0)) & 31u) == 0) {
+        // 8 points per lane and step: each 32-byte load fills one sector
+        const uint32_t base8 = p0 & ~7u;
+        const uint32_t groups8 = (p1 - base8 + 7u) >> 3;
+        const uint32_t per8 = (groups8 + 31u) >> 5;
+        const uint32_t r0 = min(lane * per8, groups8), r1 = min(r0 + per8, groups8);
+        const uint4 zero = make_uint4(0, 0, 0, 0);
+        for (uint32_t q = r0; q < r1; ++q) {
+            const uint32_t g = base8 + 8u * q;
+            uint4 a0, a1, b0 = zero, b1 = zero, c0, c1;
+            ld_words8(c.w1 + g, a0, a1);
+            if (K >= 2) ld_words8(c.w2 + g, b0, b1);
+            ld_words8(c.color + g, c0, c1);
+            group(g, a0, b0, zero, c0);
+            if (g + 4u < p1) group(g + 4u, a1, b1, zero, c1);
+        }
+    } else {
+        for (uint32_t q = q0; q < q1; ++q) {
+            const uint32_t g = base + 4u * q;
+            const uint4 q1w = ld_words<false>(c.w1 + g);
+            uint4 q2w = make_uint4(0, 0, 0, 0), q3w = make_uint4(0, 0, 0, 0);
+            if (K >= 2) q2w = ld_words<false>(c.w2 + g);
+            if (K >= 3) q3w = ld_words<false>(c.w3 + g);
+            const uint4 col = ld_words<false>(c.color + g);
+            group(g, q1w, q2w, q3w, col);
         }
     }
     shade_flush<MODE>(run, sb, pend);
