@@ -1748,10 +1748,11 @@ __device__ __forceinline__ uint32_t shade_segment_k(const CloudView& c, const Vi
 // LAYOUTS: the sum layouts of the launch's shaded views (1 two-word, 2 packed,
 // 3 both), so that a launch of one layout carries only its own code; 0 is the
 // second pass for packed views, which returns at once unless one of its views
-// flagged a pixel.
+// flagged a pixel. ONE: a launch of one view (index 0), whose parameters the
+// compiler then reads as constant operands instead of loading them per use.
 // Four blocks of 256 threads per SM (64 registers): the kernel waits on loads
 // and on the visibility reads at run starts, and more warps hide more of it.
-template <int LAYOUTS>
+template <int LAYOUTS, bool ONE>
 __global__ void __launch_bounds__(256, 4) k_shade(CloudView c, ViewTable vt, uint32_t view_base, Scratch s,
                         uint32_t shade_mask) {
     constexpr bool FALLBACK = LAYOUTS == 0;
@@ -1783,7 +1784,8 @@ __global__ void __launch_bounds__(256, 4) k_shade(CloudView c, ViewTable vt, uin
         const pc_batch bt = c.batches[e.batch];
         const uint32_t p0 = bt.first + e.seg_first;
         for (uint32_t mm = e.view_mask & shade_mask; mm; mm &= mm - 1) {
-            const uint32_t v = __ffs(mm) - 1;
+            // one view: its index is a constant, so its parameters are operands
+            const uint32_t v = ONE ? 0u : __ffs(mm) - 1;
             const ViewConst vc = make_view_const(vt.v[v]);
             const FastView fv = make_fast_view(vt.v[v]);
             const int k = (int)((e.kcodes >> (2 * v)) & 3u);
@@ -2001,9 +2003,17 @@ template <int LAYOUTS>
 static cudaError_t launch_shade_kernel(const CloudView& c, const ViewTable& vt, uint32_t view_base,
                                        Scratch s, int threads, uint32_t mask, cudaStream_t st) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<LAYOUTS>, threads, 0);
+    if constexpr (LAYOUTS != 3) {   // one view: the kernel with its index fixed
+        if (vt.n == 1) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<LAYOUTS, true>, threads, 0);
+            const int blocks = num_sms() * (nb > 0 ? nb : 1);
+            k_shade<LAYOUTS, true><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
+            return cudaGetLastError();
+        }
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<LAYOUTS, false>, threads, 0);
     const int blocks = num_sms() * (nb > 0 ? nb : 1);
-    k_shade<LAYOUTS><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
+    k_shade<LAYOUTS, false><<<blocks, threads, 0, st>>>(c, vt, view_base, s, mask);
     return cudaGetLastError();
 }
 
