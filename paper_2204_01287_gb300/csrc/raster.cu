@@ -1513,6 +1513,12 @@ __device__ __forceinline__ void ld_words8(const uint32_t* p, uint4& a, uint4& b)
                  : "l"(p));
 }
 
+// Compile-time flag of a 4-point group of the colour pass: all four points lie
+// inside the segment (no per-point range tests).
+template <bool B>
+struct IntTag {
+    static constexpr bool value = B;
+};
 // Running sums of one lane: the pixel of its current run of points, that
 // pixel's depth limit fl(w_min * 1.01f) and (second pass) its fallback flag.
 struct ShadeRun {
@@ -1559,8 +1565,10 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
     pend.n = 0;
     pend.pix = 0;
     uint32_t n_blend = 0;
-    auto group = [&](uint32_t g, const uint4& q1w, const uint4& q2w, const uint4& q3w,
-                     const uint4& col) {
+    // one group of 4 points; interior (an IntTag): all four lie inside [p0, p1)
+    auto group = [&](auto interior, uint32_t g, const uint4& q1w, const uint4& q2w,
+                     const uint4& q3w, const uint4& col) {
+        constexpr bool INTERIOR = decltype(interior)::value;
         uint32_t pix[4], w[4], bx[4], by[4];
         bool live[4];
         if (FAST) {
@@ -1589,7 +1597,7 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
             for (int j = 0; j < 4; ++j) {
                 // inside the view by the certificate; the index is clamped all the same
                 pix[j] = min(by[j] * fv.width + bx[j] + fv.pixbias, fv.npix - 1u);
-                live[j] = (uint32_t)j >= lo && (uint32_t)j < hi;
+                live[j] = INTERIOR || ((uint32_t)j >= lo && (uint32_t)j < hi);
                 w[j] = __float_as_uint(cw[j]);
             }
         } else {
@@ -1708,8 +1716,13 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
             ld_words8(c.w1 + g, a0, a1);
             if (K >= 2) ld_words8(c.w2 + g, b0, b1);
             ld_words8(c.color + g, c0, c1);
-            group(g, a0, b0, zero, c0);
-            if (g + 4u < p1) group(g + 4u, a1, b1, zero, c1);
+            if (g >= p0 && g + 8u <= p1) {   // both groups inside the segment
+                group(IntTag<true>{}, g, a0, b0, zero, c0);
+                group(IntTag<true>{}, g + 4u, a1, b1, zero, c1);
+            } else {
+                group(IntTag<false>{}, g, a0, b0, zero, c0);
+                if (g + 4u < p1) group(IntTag<false>{}, g + 4u, a1, b1, zero, c1);
+            }
         }
     } else {
         for (uint32_t q = q0; q < q1; ++q) {
@@ -1719,7 +1732,7 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
             if (K >= 2) q2w = ld_words<false>(c.w2 + g);
             if (K >= 3) q3w = ld_words<false>(c.w3 + g);
             const uint4 col = ld_words<false>(c.color + g);
-            group(g, q1w, q2w, q3w, col);
+            group(IntTag<false>{}, g, q1w, q2w, q3w, col);
         }
     }
     shade_flush<MODE>(run, sb, pend);
