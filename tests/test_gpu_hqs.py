@@ -76,13 +76,15 @@ def test_blending_changes_the_image(world):
     assert ctx.stats()["points_blended"] > 2 * int((ovis != O.EMPTY).sum())
 
 
-def test_unit_cube_ragged_batches(cuda_lib):
-    """Batches of 1000 points (not a multiple of the 4-point groups) with a
-    ragged tail, every precision forced in turn."""
+@pytest.mark.parametrize("batch", [1000, 1003])
+def test_unit_cube_ragged_batches(cuda_lib, batch):
+    """Batches of 1000 points (a ragged tail) and of 1003 points (batches that
+    start at any offset, not at a multiple of the 4- or 8-point groups), every
+    precision forced in turn."""
     import torch
     n = 3 * 10240 + 77
     xyz, rgba = S.unit_cube(n, seed=9)
-    enc = O.encode(xyz, rgba, 1000)
+    enc = O.encode(xyz, rgba, batch)
     with pcr.Context(0) as ctx:
         cloud = ctx.upload_encoded(enc.batches, enc.w1, enc.w2, enc.w3, enc.color)
         for k in (1, 2, 3):
