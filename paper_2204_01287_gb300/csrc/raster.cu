@@ -1632,10 +1632,10 @@ __device__ __forceinline__ uint32_t shade_segment(const CloudView& c, const View
             }
         }
         if (MODE == ShadeMode::kTwoWord) {
-            // Straight-line form of the run walk below, without branches: a
-            // point that starts a run flushes the lane's sums (two predicated
-            // reductions, skipped when the run blended nothing) and takes its
-            // pixel's limit; every point adds its colour when it passes.
+            // Straight-line form of the run walk below, with no branch at run
+            // starts: a point that starts a run flushes the lane's sums (two
+            // predicated reductions, skipped when the run blended nothing) and
+            // takes its pixel's limit; every point adds its colour when it passes.
             const uint32_t cc[4] = {col.x, col.y, col.z, col.w};
             bool st[4];
             uint32_t wm[4];
